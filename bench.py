@@ -1,0 +1,395 @@
+#!/usr/bin/env python
+"""Benchmark of the OS-LALM hot path on the 2D fan-beam PWLS workload
+(512x512 image, 984 views x 888 channels, M = 24 subsets, 50 iterations,
+FP16 storage of W and of the SQS denominator).
+
+One step = one reconstruction: reset x to the initial image, oslalm_init
+(first subset gradient, split gradient, rho = 1), then 50 iterations
+(1200 subset-iterations).  The metric is subset-iterations per second (one
+subset-iteration = one forward projection + exact-transpose back-projection
+of a 41-view subset plus the fused update).  Also reported: time to reach
+1 HU RMS difference from a converged image, the roofline of the dominant
+kernel, an end-to-end figure through the C ABI with host buffers, and the
+FP64 oracle timed on the host cores.
+
+--impl reference times the FP64 oracle on the same workload (bounded sample:
+one subset-iteration per step).  With torchrun (N > 1) every rank runs an
+independent replica on its own GPU (the path has no exchange step).
+"""
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "A/A' subset-iters/s (OS-LALM, 2D fan beam 512^2, 984x888, M=24)"
+UNIT = "subset-iters/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-time-to-hu", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        self.proc.wait()
+        sm, smax, reasons = [], [], set()
+        for line in open(self.path):
+            f = [t.strip() for t in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, val in zip(["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"], f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        os.unlink(self.path)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def intersections_per_subset(geom, M):
+    """Number of (ray, pixel) pairs with a non-zero length, per subset on
+    average: for each ray clipped to the image box, the pixels it crosses are
+    1 + (column crossings) + (row crossings)."""
+    from paper_1402_4381_gb300 import synth
+    org, d = synth.rays(geom)
+    org, d = org[..., :2].reshape(-1, 2), d[..., :2].reshape(-1, 2)
+    lo = np.array([-geom.nx * geom.dx / 2, -geom.ny * geom.dy / 2])
+    hi = -lo
+    with np.errstate(divide="ignore", invalid="ignore"):
+        t0 = np.full(len(org), -np.inf)
+        t1 = np.full(len(org), np.inf)
+        for k in range(2):
+            a = (lo[k] - org[:, k]) / d[:, k]
+            b = (hi[k] - org[:, k]) / d[:, k]
+            t0 = np.maximum(t0, np.minimum(a, b))
+            t1 = np.minimum(t1, np.maximum(a, b))
+    ok = t1 > t0
+    pe = org[ok] + t0[ok, None] * d[ok]
+    px = org[ok] + t1[ok, None] * d[ok]
+    pix = np.array([geom.dx, geom.dy])
+    ie = np.floor((np.clip(pe, lo, hi - 1e-9) - lo) / pix)
+    ix = np.floor((np.clip(px, lo, hi - 1e-9) - lo) / pix)
+    n = np.sum(np.abs(ix - ie), axis=1) + 1
+    return float(n.sum()) / M
+
+
+def roi_mask(geom):
+    """Field-of-view disk (pixels whose centre the fan of rays covers)."""
+    ix = (np.arange(geom.nx) - (geom.nx - 1) / 2.0) * geom.dx
+    iy = (np.arange(geom.ny) - (geom.ny - 1) / 2.0) * geom.dy
+    Y, X = np.meshgrid(iy, ix, indexing="ij")
+    R = geom.dso * math.sin(geom.ns * geom.ds / 2.0 / geom.dsd)
+    return (np.sqrt(X * X + Y * Y) <= R)[None]
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        return None
+
+
+# ---------------------------------------------------------------------------- reference arm: the FP64 oracle
+
+def oracle_sample(wl, scan, x0, n_steps):
+    """Time the FP64 oracle's subset-iterations on the workload: returns
+    (seconds per subset-iteration list, description)."""
+    from oracle import oslalm as O
+    from oracle import siddon
+    g = wl.geom
+    data, _ = O.ct_subset_data(g, scan["y"].astype(np.float64), scan["w"].astype(np.float64), wl.M, siddon)
+    # timing sample only: D approximated from one subset (M A_0' W_0 A_0 1)
+    m0 = O.bit_reversal_order(wl.M)[0]
+    D = wl.M * data.At_m(data.w[m0] * data.A_m(np.ones(g.image_shape), m0), m0)
+    alg = O.OsLalm(data, D, wl.beta, wl.delta, wl.nbr)
+    alg.init(x0.astype(np.float64))
+    times = []
+    for _ in range(n_steps):
+        t = time.perf_counter()
+        alg.step()
+        times.append(time.perf_counter() - t)
+    return times
+
+
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return 0
+    from paper_1402_4381_gb300 import workloads as W
+    wl = W.c1_fan()
+    scan = wl.make_scan()
+    x0 = np.where(roi_mask(wl.geom), 0.01, 0.0)
+    times = oracle_sample(wl, scan, x0, args.warmup + args.steps)
+    t = sum(times[args.warmup:])
+    value = args.steps / t
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * t / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl.name, "step": "one subset-iteration of the FP64 oracle", "M": wl.M},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{args.steps} timed subset-iterations (41 views x 888 rays), single thread"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------- our arm
+
+def run_ours(args):
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    from paper_1402_4381_gb300 import oslalm, workloads as W
+
+    wl = W.c1_fan()
+    if world > 1:  # independent replicas: a different noise realisation per rank
+        wl.noise_seed += 1000 * rank
+    g = wl.geom
+    scan = wl.make_scan()
+    mask_np = roi_mask(g)
+    x0_np = np.where(mask_np, 0.01, 0.0).astype(np.float32)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    y = torch.as_tensor(scan["y"], device=dev)
+    w = torch.as_tensor(scan["w"], device=dev)
+    x0 = torch.as_tensor(x0_np, device=dev)
+    x = x0.clone()
+    geom = oslalm.Geometry(g)
+    prob = oslalm.Problem(geom, y, w, beta=wl.beta, delta=wl.delta, nbr=wl.nbr, M=wl.M,
+                          w_dtype=wl.w_dtype, d_dtype=wl.d_dtype, use_graph=True)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
+
+    def step():
+        x.copy_(x0)
+        prob.init(x)
+        prob.iterate(x, wl.n_iter)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    total_ms = 0.0
+    for _ in range(args.steps):
+        flush.zero_()  # L2 flush between timed steps (outside the events)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        e1.synchronize()
+        total_ms += e0.elapsed_time(e1)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = sampler.stop()
+    t_max = total_ms
+    if world > 1:
+        tt = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_max = float(tt.item())
+    units_per_step = wl.n_iter * wl.M
+    value = world * args.steps * units_per_step / (t_max / 1000.0)
+
+    # ---- end to end through the C ABI with host buffers
+    y_h = torch.as_tensor(scan["y"]).pin_memory()
+    w_h = torch.as_tensor(scan["w"]).pin_memory()
+    x0_h = torch.as_tensor(x0_np).pin_memory()
+    x_out = torch.empty_like(x0_h).pin_memory()
+    y_d, w_d = torch.empty_like(y), torch.empty_like(w)
+
+    def e2e_step():
+        y_d.copy_(y_h, non_blocking=True)
+        w_d.copy_(w_h, non_blocking=True)
+        x.copy_(x0_h, non_blocking=True)
+        prob.set_data(y_d, w_d)
+        prob.init(x)
+        prob.iterate(x, wl.n_iter)
+        x_out.copy_(x, non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    e2e_ms = 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        e2e_step()
+        e1.record(stream)
+        e1.synchronize()
+        e2e_ms += e0.elapsed_time(e1)
+    e2e_value = args.steps * units_per_step / (e2e_ms / 1000.0)
+    h2d = y_h.numel() * 4 + w_h.numel() * 4 + x0_h.numel() * 4
+    d2h = x_out.numel() * 4
+
+    # ---- per-kernel device time (CUDA events around each launch kind)
+    x.copy_(x0)
+    prob.init(x)
+    prof = prob.profile_iterate(x, 4)
+    nl = prof["launches"][0]
+    per = {"update": prof["update"] / nl, "forward": prof["forward"] / nl, "backproject": prof["backproject"] / nl}
+    dom = max(per, key=per.get)
+    pk = peaks()
+    inter = intersections_per_subset(g, wl.M)
+    sm_mhz = clocks.get("sm_mhz") or 2070.0
+    if dom in ("forward", "backproject"):
+        ops = 3.0 * inter  # FP32 ops per (ray, pixel) pair: crossing, length, multiply-accumulate
+        peak_ops = 152 * 128 * sm_mhz * 1e6
+        achieved = ops / (per[dom] / 1000.0)
+        roof = {"kernel": {"forward": "fp2d_kernel", "backproject": "bp2d_kernel"}[dom], "bound": "alu",
+                "achieved": achieved / 1e12, "peak": peak_ops / 1e12, "unit": "TFLOP/s",
+                "frac": achieved / peak_ops, "traffic": None,
+                "work_per_launch": f"{inter:.4g} intersections x 3 FP32 ops",
+                "peak_basis": f"152 SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz (median SM clock under load)"}
+    else:
+        bytes_px = 4 + 4 + 4 + 2 + 4  # x, zeta, g read; D (fp16) read; x+ write
+        traffic = bytes_px * g.nx * g.ny
+        achieved = traffic / (per[dom] / 1000.0)
+        hbm = (pk or {}).get("hbm_gbs", 6800.0) * 1e9
+        roof = {"kernel": "update2d_kernel", "bound": "hbm", "achieved": achieved / 1e9, "peak": hbm / 1e9,
+                "unit": "GB/s", "frac": achieved / hbm, "traffic": None}
+    roof["per_kernel_ms"] = {k: round(v, 5) for k, v in per.items()}
+
+    # ---- time to 1 HU against a converged image (M = 1 continuation, long run)
+    ttu = None
+    if not args.no_time_to_hu:
+        ttu = time_to_hu(torch, oslalm, wl, geom, y, w, x0, mask_np, dev, stream)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": wl.name, "image": [g.nx, g.ny], "views": g.nviews, "channels": g.ns, "M": wl.M,
+                   "iterations_per_step": wl.n_iter, "storage": {"W": wl.w_dtype, "D": wl.d_dtype},
+                   "parallelism": f"replicas{world}", "l2": "flushed between timed steps (256 MB write)"},
+        "gpu_launches": args.steps * (wl.n_iter * wl.M * 3 + 2),
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "roofline": roof, "clocks": clocks,
+    }
+    if ttu:
+        line["time_to_1hu"] = ttu
+    if rank == 0 and not args.no_cpu_baseline:
+        times = oracle_sample(wl, scan, x0_np, 5)
+        t = sum(times[1:])
+        line["cpu_baseline"] = {"value": len(times[1:]) / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": "4 subset-iterations (41 views x 888 rays) of the same scan, FP64, "
+                                          "single thread, after one untimed"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def time_to_hu(torch, oslalm, wl, geom, y, w, x0, mask_np, dev, stream, hu_target=1.0, n_star=1500):
+    """Converged image x*: M = 1 continuation (convergent, Sec. III-A) for
+    n_star iterations in FP32 storage; then the benchmark configuration from
+    x0, timing each iteration with CUDA events until RMSD(x, x*) <= 1 HU."""
+    HU = 0.0192 / 1000.0
+    pstar = oslalm.Problem(geom, y, w, beta=wl.beta, delta=wl.delta, nbr=wl.nbr, M=1, use_graph=True)
+    xs = x0.clone()
+    pstar.init(xs)
+    pstar.iterate(xs, n_star)
+    xs_prev = xs.clone()
+    pstar.iterate(xs, 100)
+    mask = torch.as_tensor(mask_np.astype(np.uint8), device=dev)
+    tail = oslalm.rmsd(xs, xs_prev, mask) / HU  # change over the last 100 iterations
+    pstar.close()
+    prob = oslalm.Problem(geom, y, w, beta=wl.beta, delta=wl.delta, nbr=wl.nbr, M=wl.M,
+                          w_dtype=wl.w_dtype, d_dtype=wl.d_dtype, use_graph=True)
+    x = x0.clone()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    prob.init(x)
+    e1.record(stream)
+    e1.synchronize()
+    t_ms = e0.elapsed_time(e1)
+    curve = []
+    reached = None
+    for k in range(1, wl.n_iter + 1):
+        e0.record(stream)
+        prob.iterate(x, 1)
+        e1.record(stream)
+        e1.synchronize()
+        t_ms += e0.elapsed_time(e1)
+        r = oslalm.rmsd(x, xs, mask) / HU
+        curve.append(round(r, 4))
+        if reached is None and r <= hu_target:
+            reached = (k, t_ms / 1000.0)
+    prob.close()
+    return {"target_hu": hu_target, "iterations": reached[0] if reached else None,
+            "seconds": reached[1] if reached else None, "rmsd_hu_per_iteration": curve,
+            "reference": f"M=1 continuation, {n_star}+100 iterations; change over the last 100: {tail:.4f} HU",
+            "includes": "oslalm_init (first subset gradient; D cached) and the iterations; x0 = 0.01/mm in the FOV"}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

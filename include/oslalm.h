@@ -1,0 +1,217 @@
+/*
+ * liboslalm -- C ABI of the GB300 (sm_103a) OS-LALM reconstruction library.
+ *
+ * Nien & Fessler, "Fast X-ray CT image reconstruction using the linearized
+ * augmented Lagrangian method with ordered subsets" (OS-LALM).  The library
+ * solves the penalized weighted least-squares problem of Sec. IV
+ * (Eq. ct_recon)
+ *
+ *     x_hat = argmin_{x >= 0} 1/2 ||y - A x||_W^2 + R(x),
+ *     R(x)  = beta sum_{j<k neighbours} w_jk psi(x_j - x_k),
+ *     psi(t) = delta^2 (sqrt(1 + (t/delta)^2) - 1),
+ *
+ * with the OS-LALM iterates of Eq. os_lalm_iterates, the diagonal majorizer
+ * L_diag = diag{A' W A 1} and bit-reversal subset order of Sec. IV-A, and the
+ * deterministic downward continuation of Sec. III-B (Eq. rho_l_formula_qp,
+ * restart when the indicator of Eq. period_indicator_qp is positive).
+ *
+ * Conventions for every entry point:
+ *  - Return value: OSLALM_OK (0) or a negative OSLALM_ERR_* code; nothing
+ *    aborts or throws across the ABI.  oslalm_last_error() gives a message
+ *    for the calling thread's most recent failure.
+ *  - Device pointers ("dev") are allocated and owned by the caller, must stay
+ *    valid until the work queued on `stream` has finished, and are only read
+ *    or written on `stream` (a cudaStream_t passed as void*; NULL = legacy
+ *    default stream).  Calls are asynchronous on that stream unless stated.
+ *  - Host pointers ("host") are read or written before the call returns.
+ *  - Layouts: image [nz][ny][nx] (x fastest), FP32; sinogram
+ *    [view][row][channel] (channel fastest), FP32.  Units: mm, radians, 1/mm.
+ *  - Opaque handles own their device buffers; *_destroy frees them.  A handle
+ *    may be used from one host thread at a time.
+ *
+ * Scan geometry (the paper leaves the system matrix unspecified; Sec. IV):
+ *  - view v has angle phi_v = pi tau_v, tau_v = angle_start/pi +
+ *    v (angle_span/pi)/nviews, with cos/sin evaluated by exact quarter-turn
+ *    reduction; u = (cos phi, sin phi) is the beam direction,
+ *    e = (-sin phi, cos phi) the detector's lateral axis;
+ *  - PAR2D: ray c is the line through s_c e along u,
+ *    s_c = (c - (ns-1)/2 + offset_s) ds;
+ *  - FAN2D_ARC: source at -dso u, channel angle gamma_c = s_c / dsd, ray
+ *    direction cos(gamma_c) u + sin(gamma_c) e;
+ *  - CONE3D_FLAT: source at (-dso u, 0), cell centre (dsd-dso) u + s_c e +
+ *    t_t z, t_t = (t - (nt-1)/2 + offset_t) dt;
+ *  - pixel (ix,iy,iz) centred at ((ix-(nx-1)/2) dx + offset_x, ...);
+ *  - a_ij = length of ray i inside pixel j (exact ray/pixel intersection);
+ *    pixels are half-open boxes [lo, hi).
+ */
+#ifndef OSLALM_H
+#define OSLALM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define OSLALM_OK 0
+#define OSLALM_ERR_ARG (-1)     /* invalid argument, shape or handle */
+#define OSLALM_ERR_CUDA (-2)    /* a CUDA runtime call or kernel launch failed */
+#define OSLALM_ERR_RANGE (-3)   /* value outside the supported range */
+#define OSLALM_ERR_TIMEOUT (-4) /* a bounded device-side wait gave up */
+#define OSLALM_ERR_STATE (-5)   /* call out of order (e.g. iterate before init) */
+#define OSLALM_ERR_ALLOC (-6)   /* device or host allocation failed */
+
+#define OSLALM_PAR2D 0
+#define OSLALM_FAN2D_ARC 1
+#define OSLALM_CONE3D_FLAT 2
+
+#define OSLALM_F32 0
+#define OSLALM_F16 1
+#define OSLALM_BF16 2
+
+#define OSLALM_RHO_CONTINUATION 0 /* Sec. III-B downward continuation */
+#define OSLALM_RHO_FIXED 1        /* fixed rho (rho = 1: ordered-subsets SQS) */
+#define OSLALM_RHO_REPLAY 2       /* continuation with restarts read from a list */
+
+#define OSLALM_CURV_HUBER 0 /* D_R from psi'(t)/t at the current x */
+#define OSLALM_CURV_MAX 1   /* D_R from the maximum curvature psi''(0) = 1 */
+
+typedef struct oslalm_geom_desc {
+    int kind;                         /* OSLALM_PAR2D | OSLALM_FAN2D_ARC | OSLALM_CONE3D_FLAT */
+    int nx, ny, nz;                   /* image size; nz = 1 for 2D */
+    double dx, dy, dz;                /* pixel size (mm) */
+    double offset_x, offset_y, offset_z; /* image centre (mm) */
+    int nviews;
+    double angle_start, angle_span;   /* radians */
+    int ns, nt;                       /* channels, detector rows (nt = 1 for 2D) */
+    double ds, dt;                    /* channel / row pitch (mm at the detector) */
+    double offset_s, offset_t;        /* detector offsets in channels / rows */
+    double dso, dsd;                  /* source-isocentre, source-detector (mm) */
+} oslalm_geom_desc;
+
+typedef struct oslalm_params {
+    double beta;      /* regularization weight */
+    double delta;     /* hyperbola edge parameter (1/mm) */
+    int nbr;          /* 4 or 8 (2D); 6 or 26 (3D); w_jk = 1/index distance */
+    int M;            /* number of ordered subsets (views v with v mod M = m) */
+    double rho_min;   /* continuation floor (Sec. III-B uses 1e-3) */
+    int n_inner;      /* inner FISTA steps of the constrained denoising; 1 */
+    int rho_mode;     /* OSLALM_RHO_* */
+    double rho_fixed; /* rho for OSLALM_RHO_FIXED */
+    int curvature;    /* OSLALM_CURV_* */
+    int w_dtype;      /* storage of W: OSLALM_F32 | OSLALM_F16 | OSLALM_BF16 */
+    int d_dtype;      /* storage of the SQS denominator D: same choices */
+    int use_graph;    /* 1: replay whole iterations from a captured CUDA graph */
+} oslalm_params;
+
+/* One record per subset-iteration (filled by oslalm_iterate when asked). */
+typedef struct oslalm_stats {
+    double xi;        /* restart indicator of Eq. period_indicator_qp (subset gradients) */
+    double rho_used;  /* rho of this subset-iteration */
+    int l;            /* continuation counter after the update */
+    int restart;      /* 1 if l was reset */
+    int subset;       /* subset whose gradient was computed (sigma(j+1)) */
+    int pad;
+} oslalm_stats;
+
+typedef struct oslalm_geom oslalm_geom;
+typedef struct oslalm_problem oslalm_problem;
+
+/* Message of the calling thread's last failure ("" if none).  Never NULL. */
+const char *oslalm_last_error(void);
+
+/* Library ABI version (major*100 + minor). */
+int oslalm_version(void);
+
+/* ---- geometry / system model -------------------------------------------
+ * Builds the per-ray parameter tables on the current CUDA device (host FP64
+ * set-up, one synchronous upload).  Requires the image box to lie strictly
+ * between source and detector (fan/cone) and nx, ny, nz, nviews, ns, nt > 0.
+ * Errors: ARG (bad descriptor), ALLOC, CUDA.  *out is NULL on failure. */
+int oslalm_geom_create(const oslalm_geom_desc *desc, oslalm_geom **out);
+int oslalm_geom_destroy(oslalm_geom *g);
+
+/* ---- subsets (Sec. IV-A bit-reversal order; Sec. IV-B interleaved views) --
+ * order[host, M]: subset visiting order by bit reversal; for M not a power of
+ * two the bit-reversed values of 0..2^ceil(log2 M)-1 that are < M.
+ * views[host, capacity ceil(nviews/M)]: views of subset m (v = m, m+M, ...);
+ * *n receives their count.  Errors: ARG. */
+int oslalm_subset_order(int M, int *order);
+int oslalm_subset_views(const oslalm_geom *g, int M, int m, int *views, int *n);
+
+/* ---- projector pair (A_m and its exact transpose) -------------------------
+ * oslalm_project: sino[dev, nv][nt][ns] = A_views x[dev, image].
+ * oslalm_backproject: x[dev, image] (=|+=) A_views' sino[dev, nv][nt][ns]
+ *   (accumulate = 0 overwrites, 1 adds).
+ * views[dev, nv]: global view indices (each in [0, nviews)); nv >= 0 (0 is a
+ * no-op / zero image).  The back-projector evaluates the same per-ray/pixel
+ * weights as the projector, so it is the transpose up to summation order.
+ * Errors: ARG, CUDA. */
+int oslalm_project(const oslalm_geom *g, const float *x, float *sino,
+                   const int *views, int nv, void *stream);
+int oslalm_backproject(const oslalm_geom *g, const float *sino, float *x,
+                       const int *views, int nv, int accumulate, void *stream);
+
+/* ---- PWLS problem and OS-LALM (Eq. os_lalm_iterates, Sec. III-IV) --------
+ * oslalm_problem_create: copies y[dev, sino] and w[dev, sino] (FP32,
+ *   w >= 0) into library-owned subset-major buffers, storing W as
+ *   params->w_dtype (FP16/BF16 with a power-of-two per-array scale).  The
+ *   problem keeps a reference to g (g must outlive it).  Synchronizes the
+ *   current device once.  Errors: ARG, RANGE, ALLOC, CUDA.
+ * oslalm_problem_set_data: replaces y and W (same shapes) on `stream`; the
+ *   SQS denominator is recomputed by the next oslalm_init only.
+ * oslalm_init: on `stream`, computes D = A'WA1 (first call or after
+ *   set_data), zeta = M grad l_{sigma(0)}(x) (Eq. os_lalm_iterates), g = zeta,
+ *   l = 0, rho = 1 (or rho_fixed).  x[dev, image] is read only.
+ * oslalm_iterate: runs n_iter full iterations (n_iter*M subset-iterations)
+ *   updating x[dev, image] in place; each subset-iteration is the inner SQS
+ *   step with the hyperbola regularizer and the non-negativity projection,
+ *   the forward projection with the weighted residual, the exact-transpose
+ *   back-projection with the split-gradient update and the restart
+ *   indicator, and the continuation update (rho lives on the device, no host
+ *   round trip).  stats[host, n_iter*M] or NULL: when given, the call
+ *   synchronizes `stream` and fills one record per subset-iteration.
+ *   Errors: STATE (no init), ARG, CUDA.
+ * oslalm_set_replay: restart decisions for OSLALM_RHO_REPLAY, restarts[host,
+ *   n] (0/1) indexed by the global subset-iteration counter; copied.
+ * oslalm_cost: *out[host] = Psi(x) = 1/2 sum_i w_i (y_i - [Ax]_i)^2 + R(x),
+ *   projections accumulated and reduced in FP64; synchronizes `stream`.
+ * oslalm_get_state / oslalm_set_state: the iteration state for an exact
+ *   resume: g and zeta [dev, image each, FP32], *rho_l_j[host, 3 doubles] =
+ *   {rho, l, j} (j = subset-iterations done).  Both synchronize `stream`. */
+int oslalm_problem_create(const oslalm_geom *g, const float *y, const float *w,
+                          const oslalm_params *params, oslalm_problem **out);
+int oslalm_problem_destroy(oslalm_problem *p);
+int oslalm_problem_set_data(oslalm_problem *p, const float *y, const float *w, void *stream);
+int oslalm_init(oslalm_problem *p, const float *x, void *stream);
+int oslalm_iterate(oslalm_problem *p, float *x, int n_iter, oslalm_stats *stats, void *stream);
+int oslalm_set_replay(oslalm_problem *p, const int *restarts, int n);
+int oslalm_cost(oslalm_problem *p, const float *x, double *out, void *stream);
+int oslalm_get_state(oslalm_problem *p, float *g, float *zeta, double *rho_l_j, void *stream);
+int oslalm_set_state(oslalm_problem *p, const float *g, const float *zeta, const double *rho_l_j, void *stream);
+
+/* The SQS denominator D = A'WA1 as stored (dequantized to FP32) into
+ * d[dev, image]; valid after oslalm_init.  Errors: STATE, CUDA. */
+int oslalm_get_denominator(oslalm_problem *p, float *d, void *stream);
+
+/* Timing pass for roofline reports: runs n_iter full iterations exactly as
+ * oslalm_iterate does without a graph, with CUDA events recorded on `stream`
+ * around every kernel launch, and returns the summed device time (ms) per
+ * kernel kind in ms_out[host, 3] = {update, forward+residual,
+ * back-projection+split-gradient}; launches_out[host, 3] receives the launch
+ * counts.  Synchronizes `stream`.  Errors: STATE, ARG, CUDA. */
+int oslalm_profile_iterate(oslalm_problem *p, float *x, int n_iter, double *ms_out, int *launches_out,
+                           void *stream);
+
+/* ---- monitoring ----------------------------------------------------------
+ * *out[host] = sqrt(sum_{mask} (x - xref)^2 / count(mask)) over the pixels
+ * where mask[dev, image, uint8] != 0 (FP64 reduction); synchronizes.  Sec. V
+ * measures convergence by this RMS difference (reported in HU by callers). */
+int oslalm_rmsd(const float *x, const float *xref, const uint8_t *mask, long n,
+                double *out, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* OSLALM_H */

@@ -1,0 +1,231 @@
+// Geometry / system-model set-up, subset tables and the error model of the
+// C ABI.  Host code, FP64; the per-ray tables it uploads are what the 2D
+// projector pair reads (see common.cuh, Ray2).
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+
+#include "common.cuh"
+
+namespace oslalm {
+
+static thread_local char g_err[1024] = "";
+
+int fail(int code, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+void clear_error() { g_err[0] = 0; }
+
+bool is_3d(const oslalm_geom *g) { return g->d.kind == OSLALM_CONE3D_FLAT; }
+
+// (cos(pi t), sin(pi t)) with the quarter turn taken out exactly, so that
+// views at multiples of 90 degrees are exactly axis-aligned.
+static void cos_sin_turns(double t, double *c, double *s) {
+    double n = floor(2.0 * t + 0.5);
+    double r = t - 0.5 * n;
+    double cr = cos(M_PI * r), sr = sin(M_PI * r);
+    double q = fmod(n, 4.0);
+    if (q < 0) q += 4.0;
+    if (q == 0.0) { *c = cr; *s = sr; }
+    else if (q == 1.0) { *c = -sr; *s = cr; }
+    else if (q == 2.0) { *c = -cr; *s = -sr; }
+    else { *c = sr; *s = -cr; }
+}
+
+static double view_turns(const oslalm_geom_desc &d, int v) {
+    return d.angle_start / M_PI + (double)v * (d.angle_span / M_PI) / (double)d.nviews;
+}
+
+// Parameters of the 2D line through P with unit direction (dx_, dy_).
+static Ray2 make_ray2(const oslalm_geom_desc &d, double px, double py, double ux, double uy) {
+    const double xlo = d.offset_x - 0.5 * d.nx * d.dx;
+    const double ylo = d.offset_y - 0.5 * d.ny * d.dy;
+    const double ax = ux / d.dx, ay = uy / d.dy;  // direction in index units
+    Ray2 r;
+    int axis;
+    double kappa, lrow, b0;
+    if (fabs(ax) >= fabs(ay)) {  // x-major: b = y index along a = x index
+        axis = 0;
+        kappa = ay / ax;
+        lrow = d.dx / fabs(ux);
+        double yat = py + (xlo - px) * (uy / ux);
+        b0 = (yat - ylo) / d.dy;
+    } else {
+        axis = 1;
+        kappa = ax / ay;
+        lrow = d.dy / fabs(uy);
+        double xat = px + (ylo - py) * (ux / uy);
+        b0 = (xat - xlo) / d.dx;
+    }
+    double n0 = floor(b0 + 0.5);
+    r.f0 = (float)(b0 - n0);
+    r.kappa = (float)kappa;
+    r.lrow = (float)lrow;
+    r.packed = (int)n0 * 2 + axis;
+    return r;
+}
+
+static int validate(const oslalm_geom_desc *d) {
+    if (!d) return fail(OSLALM_ERR_ARG, "geometry descriptor is NULL");
+    if (d->kind < 0 || d->kind > 2) return fail(OSLALM_ERR_ARG, "unknown geometry kind %d", d->kind);
+    if (d->nx <= 0 || d->ny <= 0 || d->nz <= 0 || d->nviews <= 0 || d->ns <= 0 || d->nt <= 0)
+        return fail(OSLALM_ERR_ARG, "sizes must be positive");
+    if (d->kind != OSLALM_CONE3D_FLAT && (d->nz != 1 || d->nt != 1))
+        return fail(OSLALM_ERR_ARG, "2D geometries need nz = nt = 1");
+    if (!(d->dx > 0 && d->dy > 0 && d->dz > 0 && d->ds > 0 && d->dt > 0))
+        return fail(OSLALM_ERR_ARG, "pixel and detector pitches must be positive");
+    if ((long)d->nx * d->ny * d->nz > (1L << 31) - 1 || (long)d->nviews * d->ns * d->nt > (1L << 31) - 1)
+        return fail(OSLALM_ERR_RANGE, "image or sinogram exceeds 2^31 elements");
+    if (d->nx > (1 << 20) || d->ny > (1 << 20) || d->nviews > (1 << 24))
+        return fail(OSLALM_ERR_RANGE, "dimension too large");
+    if (d->kind != OSLALM_PAR2D) {
+        if (!(d->dso > 0 && d->dsd > d->dso)) return fail(OSLALM_ERR_ARG, "need 0 < dso < dsd");
+        double hx = 0.5 * d->nx * d->dx + fabs(d->offset_x);
+        double hy = 0.5 * d->ny * d->dy + fabs(d->offset_y);
+        double r = sqrt(hx * hx + hy * hy);
+        if (!(r < d->dso && r < d->dsd - d->dso))
+            return fail(OSLALM_ERR_ARG, "image box (radius %.3f mm) must lie inside the source circle and before the detector", r);
+        double gmax = fabs((0.5 * d->ns + fabs(d->offset_s)) * d->ds / d->dsd);
+        if (d->kind == OSLALM_FAN2D_ARC && gmax >= 1.2)
+            return fail(OSLALM_ERR_RANGE, "fan angle too wide");
+    }
+    return 0;
+}
+
+Geo2 geo2_of(const oslalm_geom *g);
+
+}  // namespace oslalm
+
+using namespace oslalm;
+
+oslalm::Geo2 oslalm_geom::geo2() const {
+    Geo2 o;
+    o.kind = d.kind;
+    o.nx = d.nx;
+    o.ny = d.ny;
+    o.ns = d.ns;
+    o.nviews = d.nviews;
+    o.dx = (float)d.dx;
+    o.dy = (float)d.dy;
+    o.xlo = (float)(d.offset_x - 0.5 * d.nx * d.dx);
+    o.ylo = (float)(d.offset_y - 0.5 * d.ny * d.dy);
+    o.inv_ds = (float)(1.0 / d.ds);
+    o.c0 = (float)((d.ns - 1) / 2.0 - d.offset_s);
+    o.dso = (float)d.dso;
+    o.dsd = (float)d.dsd;
+    o.half_diag = (float)(0.5 * sqrt(d.dx * d.dx + d.dy * d.dy));
+    o.rays = d_rays;
+    o.views = d_views;
+    return o;
+}
+
+extern "C" {
+
+const char *oslalm_last_error(void) { return oslalm::g_err; }
+
+int oslalm_version(void) { return 100; }
+
+int oslalm_geom_create(const oslalm_geom_desc *desc, oslalm_geom **out) {
+    clear_error();
+    if (!out) return fail(OSLALM_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (int rc = validate(desc)) return rc;
+    const oslalm_geom_desc &d = *desc;
+    oslalm_geom *g = new (std::nothrow) oslalm_geom();
+    if (!g) return fail(OSLALM_ERR_ALLOC, "host allocation failed");
+    g->d = d;
+    cudaGetDevice(&g->device);
+    std::vector<View2> views(d.nviews);
+    std::vector<View3> views3(d.nviews);
+    std::vector<int> allv(d.nviews);
+    std::vector<Ray2> rays;
+    bool two_d = d.kind != OSLALM_CONE3D_FLAT;
+    if (two_d) rays.resize((size_t)d.nviews * d.ns);
+    for (int v = 0; v < d.nviews; ++v) {
+        double cu, su;
+        cos_sin_turns(view_turns(d, v), &cu, &su);
+        double ex = -su, ey = cu;
+        views[v] = View2{(float)cu, (float)su, 0.f, 0.f};
+        views3[v] = View3{(float)cu, (float)su, (float)(-d.dso * cu), (float)(-d.dso * su)};
+        allv[v] = v;
+        if (!two_d) continue;
+        for (int c = 0; c < d.ns; ++c) {
+            double s = ((double)c - (d.ns - 1) / 2.0 + d.offset_s) * d.ds;
+            double px, py, ux, uy;
+            if (d.kind == OSLALM_PAR2D) {
+                px = s * ex; py = s * ey; ux = cu; uy = su;
+            } else {
+                double gam = s / d.dsd;
+                double cg = cos(gam), sg = sin(gam);
+                px = -d.dso * cu; py = -d.dso * su;
+                ux = cg * cu + sg * ex;
+                uy = cg * su + sg * ey;
+            }
+            rays[(size_t)v * d.ns + c] = make_ray2(d, px, py, ux, uy);
+        }
+    }
+    auto cleanup = [&](int code, const char *what, cudaError_t e) {
+        cudaFree(g->d_rays); cudaFree(g->d_views); cudaFree(g->d_views3); cudaFree(g->d_allviews);
+        delete g;
+        return fail(code, "%s: %s", what, cudaGetErrorString(e));
+    };
+    cudaError_t e;
+    if ((e = cudaMalloc(&g->d_views, sizeof(View2) * d.nviews)) != cudaSuccess) return cleanup(OSLALM_ERR_ALLOC, "cudaMalloc views", e);
+    if ((e = cudaMalloc(&g->d_views3, sizeof(View3) * d.nviews)) != cudaSuccess) return cleanup(OSLALM_ERR_ALLOC, "cudaMalloc views3", e);
+    if ((e = cudaMalloc(&g->d_allviews, sizeof(int) * d.nviews)) != cudaSuccess) return cleanup(OSLALM_ERR_ALLOC, "cudaMalloc views", e);
+    if (two_d && (e = cudaMalloc(&g->d_rays, sizeof(Ray2) * rays.size())) != cudaSuccess) return cleanup(OSLALM_ERR_ALLOC, "cudaMalloc rays", e);
+    if ((e = cudaMemcpy(g->d_views, views.data(), sizeof(View2) * d.nviews, cudaMemcpyHostToDevice)) != cudaSuccess) return cleanup(OSLALM_ERR_CUDA, "upload", e);
+    if ((e = cudaMemcpy(g->d_views3, views3.data(), sizeof(View3) * d.nviews, cudaMemcpyHostToDevice)) != cudaSuccess) return cleanup(OSLALM_ERR_CUDA, "upload", e);
+    if ((e = cudaMemcpy(g->d_allviews, allv.data(), sizeof(int) * d.nviews, cudaMemcpyHostToDevice)) != cudaSuccess) return cleanup(OSLALM_ERR_CUDA, "upload", e);
+    if (two_d && (e = cudaMemcpy(g->d_rays, rays.data(), sizeof(Ray2) * rays.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return cleanup(OSLALM_ERR_CUDA, "upload", e);
+    *out = g;
+    return OSLALM_OK;
+}
+
+int oslalm_geom_destroy(oslalm_geom *g) {
+    clear_error();
+    if (!g) return OSLALM_OK;
+    cudaFree(g->d_rays);
+    cudaFree(g->d_views);
+    cudaFree(g->d_views3);
+    cudaFree(g->d_allviews);
+    delete g;
+    return OSLALM_OK;
+}
+
+int oslalm_subset_order(int M, int *order) {
+    clear_error();
+    if (M <= 0 || !order) return fail(OSLALM_ERR_ARG, "need M > 0 and an order buffer");
+    int b = 0;
+    while ((1 << b) < M) ++b;
+    int k = 0;
+    for (int i = 0; i < (1 << b); ++i) {
+        int r = 0;
+        for (int q = 0; q < b; ++q)
+            if (i & (1 << q)) r |= 1 << (b - 1 - q);
+        if (r < M) order[k++] = r;
+    }
+    return OSLALM_OK;
+}
+
+int oslalm_subset_views(const oslalm_geom *g, int M, int m, int *views, int *n) {
+    clear_error();
+    if (!g || M <= 0 || m < 0 || m >= M || !n) return fail(OSLALM_ERR_ARG, "bad subset request");
+    int k = 0;
+    for (int v = m; v < g->d.nviews; v += M) {
+        if (views) views[k] = v;
+        ++k;
+    }
+    *n = k;
+    return OSLALM_OK;
+}
+
+}  // extern "C"

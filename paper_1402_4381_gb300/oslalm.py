@@ -1,0 +1,310 @@
+"""Python binding of liboslalm (include/oslalm.h): argument marshalling only.
+
+Device memory and streams come from PyTorch tensors (``data_ptr()``) and
+``torch.cuda.current_stream()``; every computation runs in the library's CUDA
+kernels.  There is no fallback: if the library is not built or no GPU is
+present, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import List, Optional, Sequence
+
+import numpy as np
+
+from . import build as _build
+
+F32, F16, BF16 = 0, 1, 2
+_DTYPES = {"f32": F32, "f16": F16, "bf16": BF16}
+RHO_CONTINUATION, RHO_FIXED, RHO_REPLAY = 0, 1, 2
+_RHO = {"continuation": RHO_CONTINUATION, "fixed": RHO_FIXED, "replay": RHO_REPLAY}
+CURV_HUBER, CURV_MAX = 0, 1
+
+
+class OslalmError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"liboslalm error {code}: {msg}")
+        self.code = code
+
+
+class GeomDesc(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("dz", ctypes.c_double),
+                ("offset_x", ctypes.c_double), ("offset_y", ctypes.c_double), ("offset_z", ctypes.c_double),
+                ("nviews", ctypes.c_int), ("angle_start", ctypes.c_double), ("angle_span", ctypes.c_double),
+                ("ns", ctypes.c_int), ("nt", ctypes.c_int), ("ds", ctypes.c_double), ("dt", ctypes.c_double),
+                ("offset_s", ctypes.c_double), ("offset_t", ctypes.c_double),
+                ("dso", ctypes.c_double), ("dsd", ctypes.c_double)]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("beta", ctypes.c_double), ("delta", ctypes.c_double), ("nbr", ctypes.c_int), ("M", ctypes.c_int),
+                ("rho_min", ctypes.c_double), ("n_inner", ctypes.c_int), ("rho_mode", ctypes.c_int),
+                ("rho_fixed", ctypes.c_double), ("curvature", ctypes.c_int), ("w_dtype", ctypes.c_int),
+                ("d_dtype", ctypes.c_int), ("use_graph", ctypes.c_int)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("xi", ctypes.c_double), ("rho_used", ctypes.c_double), ("l", ctypes.c_int),
+                ("restart", ctypes.c_int), ("subset", ctypes.c_int), ("pad", ctypes.c_int)]
+
+
+_lib = None
+_VP = ctypes.c_void_p
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load liboslalm.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is not built: run __graft_entry__.build() (nvcc, sm_103a)")
+    L = ctypes.CDLL(path)
+    i, d, ip = ctypes.c_int, ctypes.c_double, ctypes.POINTER(ctypes.c_int)
+    sig = {
+        "oslalm_last_error": ([], ctypes.c_char_p),
+        "oslalm_version": ([], i),
+        "oslalm_geom_create": ([ctypes.POINTER(GeomDesc), ctypes.POINTER(_VP)], i),
+        "oslalm_geom_destroy": ([_VP], i),
+        "oslalm_subset_order": ([i, ip], i),
+        "oslalm_subset_views": ([_VP, i, i, ip, ip], i),
+        "oslalm_project": ([_VP, _VP, _VP, _VP, i, _VP], i),
+        "oslalm_backproject": ([_VP, _VP, _VP, _VP, i, i, _VP], i),
+        "oslalm_problem_create": ([_VP, _VP, _VP, ctypes.POINTER(Params), ctypes.POINTER(_VP)], i),
+        "oslalm_problem_destroy": ([_VP], i),
+        "oslalm_problem_set_data": ([_VP, _VP, _VP, _VP], i),
+        "oslalm_init": ([_VP, _VP, _VP], i),
+        "oslalm_iterate": ([_VP, _VP, i, ctypes.POINTER(Stats), _VP], i),
+        "oslalm_set_replay": ([_VP, ip, i], i),
+        "oslalm_cost": ([_VP, _VP, ctypes.POINTER(d), _VP], i),
+        "oslalm_get_state": ([_VP, _VP, _VP, ctypes.POINTER(d), _VP], i),
+        "oslalm_set_state": ([_VP, _VP, _VP, ctypes.POINTER(d), _VP], i),
+        "oslalm_get_denominator": ([_VP, _VP, _VP], i),
+        "oslalm_rmsd": ([_VP, _VP, _VP, ctypes.c_long, ctypes.POINTER(d), _VP], i),
+        "oslalm_profile_iterate": ([_VP, _VP, i, ctypes.POINTER(d), ip, _VP], i),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = L
+    return L
+
+
+def _check(rc, what):
+    if rc != 0:
+        msg = lib().oslalm_last_error().decode(errors="replace")
+        raise OslalmError(rc, f"{what}: {msg}")
+
+
+def _stream(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return _VP(s.cuda_stream)
+
+
+def _ptr(t):
+    return _VP(t.data_ptr()) if t is not None else _VP(0)
+
+
+def _dev_f32(t, shape=None, name="tensor"):
+    import torch
+    if not isinstance(t, torch.Tensor) or t.device.type != "cuda" or t.dtype != torch.float32 or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous float32 CUDA tensor")
+    if shape is not None and t.numel() != int(np.prod(shape)):
+        raise ValueError(f"{name} has {t.numel()} elements, expected {int(np.prod(shape))}")
+    return t
+
+
+def subset_order(M: int) -> List[int]:
+    arr = (ctypes.c_int * M)()
+    _check(lib().oslalm_subset_order(M, arr), "subset_order")
+    return list(arr)
+
+
+class Geometry:
+    """Handle of an oslalm_geom built from a ``synth.Geometry`` description."""
+
+    def __init__(self, geom):
+        self.desc_py = geom
+        d = GeomDesc()
+        for name, _ in GeomDesc._fields_:
+            setattr(d, name, getattr(geom, name))
+        self._h = _VP()
+        _check(lib().oslalm_geom_create(ctypes.byref(d), ctypes.byref(self._h)), "geom_create")
+        self._views_all = None
+
+    @property
+    def handle(self):
+        return self._h
+
+    @property
+    def image_shape(self):
+        return self.desc_py.image_shape
+
+    def sino_shape(self, nv=None):
+        g = self.desc_py
+        return (g.nviews if nv is None else nv, g.nt, g.ns)
+
+    def views_tensor(self, views=None):
+        import torch
+        if views is None:
+            if self._views_all is None:
+                self._views_all = torch.arange(self.desc_py.nviews, dtype=torch.int32, device="cuda")
+            return self._views_all
+        if isinstance(views, torch.Tensor) and views.is_cuda:
+            return views.to(torch.int32).contiguous()
+        return torch.as_tensor(np.asarray(views, dtype=np.int32), device="cuda")
+
+    def subset_views(self, M: int, m: int) -> List[int]:
+        n = ctypes.c_int()
+        arr = (ctypes.c_int * (self.desc_py.nviews // M + 1))()
+        _check(lib().oslalm_subset_views(self._h, M, m, arr, ctypes.byref(n)), "subset_views")
+        return list(arr[: n.value])
+
+    def project(self, x, views=None, out=None, stream=None):
+        import torch
+        _dev_f32(x, self.image_shape, "x")
+        vt = self.views_tensor(views)
+        nv = int(vt.numel())
+        if out is None:
+            out = torch.empty(self.sino_shape(nv), dtype=torch.float32, device=x.device)
+        _dev_f32(out, self.sino_shape(nv), "sino")
+        _check(lib().oslalm_project(self._h, _ptr(x), _ptr(out), _ptr(vt), nv, _stream(stream)), "project")
+        return out
+
+    def backproject(self, sino, views=None, out=None, accumulate=False, stream=None):
+        import torch
+        vt = self.views_tensor(views)
+        nv = int(vt.numel())
+        _dev_f32(sino, self.sino_shape(nv), "sino")
+        if out is None:
+            out = torch.empty(self.image_shape, dtype=torch.float32, device=sino.device)
+        _dev_f32(out, self.image_shape, "x")
+        _check(lib().oslalm_backproject(self._h, _ptr(sino), _ptr(out), _ptr(vt), nv, int(accumulate),
+                                        _stream(stream)), "backproject")
+        return out
+
+    def close(self):
+        if self._h:
+            lib().oslalm_geom_destroy(self._h)
+            self._h = _VP()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Problem:
+    """PWLS problem + OS-LALM state (oslalm_problem)."""
+
+    def __init__(self, geom: Geometry, y, w, *, beta, delta, nbr, M, rho_min=1e-3, rho_mode="continuation",
+                 rho_fixed=1.0, curvature="huber", w_dtype="f32", d_dtype="f32", use_graph=True, n_inner=1):
+        self.geom = geom
+        shape = geom.sino_shape()
+        _dev_f32(y, shape, "y")
+        _dev_f32(w, shape, "w")
+        p = Params()
+        p.beta, p.delta, p.nbr, p.M = float(beta), float(delta), int(nbr), int(M)
+        p.rho_min, p.n_inner = float(rho_min), int(n_inner)
+        p.rho_mode, p.rho_fixed = _RHO[rho_mode], float(rho_fixed)
+        p.curvature = CURV_HUBER if curvature == "huber" else CURV_MAX
+        p.w_dtype, p.d_dtype = _DTYPES[w_dtype], _DTYPES[d_dtype]
+        p.use_graph = int(bool(use_graph))
+        self.params = p
+        self.M = int(M)
+        self._h = _VP()
+        _check(lib().oslalm_problem_create(geom.handle, _ptr(y), _ptr(w), ctypes.byref(p), ctypes.byref(self._h)),
+               "problem_create")
+
+    def set_data(self, y, w, stream=None):
+        shape = self.geom.sino_shape()
+        _dev_f32(y, shape, "y")
+        _dev_f32(w, shape, "w")
+        _check(lib().oslalm_problem_set_data(self._h, _ptr(y), _ptr(w), _stream(stream)), "set_data")
+
+    def init(self, x, stream=None):
+        _dev_f32(x, self.geom.image_shape, "x")
+        _check(lib().oslalm_init(self._h, _ptr(x), _stream(stream)), "init")
+
+    def iterate(self, x, n_iter=1, stats=False, stream=None):
+        _dev_f32(x, self.geom.image_shape, "x")
+        buf = None
+        if stats:
+            buf = (Stats * (n_iter * self.M))()
+        _check(lib().oslalm_iterate(self._h, _ptr(x), int(n_iter), buf, _stream(stream)), "iterate")
+        if stats:
+            return [dict(xi=s.xi, rho_used=s.rho_used, l=s.l, restart=bool(s.restart), subset=s.subset) for s in buf]
+        return None
+
+    def profile_iterate(self, x, n_iter=1, stream=None):
+        """Device time (ms) per kernel kind over n_iter iterations, from CUDA
+        events around each launch: dict(update, forward, backproject, launches)."""
+        _dev_f32(x, self.geom.image_shape, "x")
+        ms = (ctypes.c_double * 3)()
+        cnt = (ctypes.c_int * 3)()
+        _check(lib().oslalm_profile_iterate(self._h, _ptr(x), int(n_iter), ms, cnt, _stream(stream)),
+               "profile_iterate")
+        return dict(update=ms[0], forward=ms[1], backproject=ms[2], launches=list(cnt))
+
+    def set_replay(self, restarts: Sequence[int]):
+        arr = (ctypes.c_int * len(restarts))(*[int(bool(r)) for r in restarts])
+        _check(lib().oslalm_set_replay(self._h, arr, len(restarts)), "set_replay")
+
+    def cost(self, x, stream=None) -> float:
+        _dev_f32(x, self.geom.image_shape, "x")
+        out = ctypes.c_double()
+        _check(lib().oslalm_cost(self._h, _ptr(x), ctypes.byref(out), _stream(stream)), "cost")
+        return out.value
+
+    def get_state(self, stream=None):
+        import torch
+        shape = self.geom.image_shape
+        g = torch.empty(shape, dtype=torch.float32, device="cuda")
+        z = torch.empty(shape, dtype=torch.float32, device="cuda")
+        s = (ctypes.c_double * 3)()
+        _check(lib().oslalm_get_state(self._h, _ptr(g), _ptr(z), s, _stream(stream)), "get_state")
+        return dict(g=g, zeta=z, rho=s[0], l=int(s[1]), j=int(s[2]))
+
+    def set_state(self, st, stream=None):
+        s = (ctypes.c_double * 3)(st["rho"], st["l"], st["j"])
+        _check(lib().oslalm_set_state(self._h, _ptr(st["g"]), _ptr(st["zeta"]), s, _stream(stream)), "set_state")
+
+    def denominator(self, stream=None):
+        import torch
+        d = torch.empty(self.geom.image_shape, dtype=torch.float32, device="cuda")
+        _check(lib().oslalm_get_denominator(self._h, _ptr(d), _stream(stream)), "get_denominator")
+        return d
+
+    def close(self):
+        if self._h:
+            lib().oslalm_problem_destroy(self._h)
+            self._h = _VP()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def rmsd(x, xref, mask, stream=None) -> float:
+    """sqrt(mean over mask of (x - xref)^2), FP64 reduction on the device."""
+    import torch
+    _dev_f32(x, None, "x")
+    _dev_f32(xref, None, "xref")
+    if mask.dtype != torch.uint8 or not mask.is_cuda:
+        raise ValueError("mask must be a uint8 CUDA tensor")
+    out = ctypes.c_double()
+    _check(lib().oslalm_rmsd(_ptr(x), _ptr(xref), _ptr(mask), int(x.numel()), ctypes.byref(out), _stream(stream)),
+           "rmsd")
+    return out.value
