@@ -131,6 +131,16 @@ int oslalm_version(void);
 int oslalm_geom_create(const oslalm_geom_desc *desc, oslalm_geom **out);
 int oslalm_geom_destroy(oslalm_geom *g);
 
+/* Host-only view of the 2D system model: the per-ray parameters that the
+ * projector pair reads for view `view` (arrays [host, ns] each).  Ray c is
+ * written along its major index axis a as b(a) = n0 + f0 + a (k/2048 +
+ * kappa_lo), with packed = (k << 16) | ((n0 & 0x7fff) << 1) | axis (axis 0:
+ * a = x index, 1: a = y index) and lrow = ray length (mm) per unit of a
+ * (0 for a ray that misses the image).  The length of the ray inside pixel
+ * (ia, jb) is lrow times the fraction of row [ia, ia+1] whose b lies in
+ * [jb, jb+1).  No GPU needed.  Errors: ARG, RANGE. */
+int oslalm_ray_table(const oslalm_geom_desc *desc, int view, float *f0, float *kappa_lo, float *lrow, int *packed);
+
 /* ---- subsets (Sec. IV-A bit-reversal order; Sec. IV-B interleaved views) --
  * order[host, M]: subset visiting order by bit reversal; for M not a power of
  * two the bit-reversed values of 0..2^ceil(log2 M)-1 that are < M.
@@ -151,6 +161,16 @@ int oslalm_project(const oslalm_geom *g, const float *x, float *sino,
                    const int *views, int nv, void *stream);
 int oslalm_backproject(const oslalm_geom *g, const float *sino, float *x,
                        const int *views, int nv, int accumulate, void *stream);
+
+/* ---- initial image ---------------------------------------------------------
+ * x[dev, image] = filtered back-projection of sino[dev, nviews][nt][ns] (all
+ * views).  The paper initialises from an FBP image (Sec. V) without giving
+ * the filter; this is the textbook analytic reconstruction: Ram-Lak parallel
+ * FBP, equiangular fan FBP over 360 degrees, Feldkamp for the flat cone
+ * detector (fan/cone need angle_span = 2 pi).  clip_nonneg = 1 clips to
+ * x >= 0.  Allocates a filtered-sinogram buffer with cudaMallocAsync on
+ * `stream` and frees it before returning.  Errors: ARG, RANGE, CUDA. */
+int oslalm_fbp(const oslalm_geom *g, const float *sino, float *x, int clip_nonneg, void *stream);
 
 /* ---- PWLS problem and OS-LALM (Eq. os_lalm_iterates, Sec. III-IV) --------
  * oslalm_problem_create: copies y[dev, sino] and w[dev, sino] (FP32,

@@ -36,16 +36,23 @@ void clear_error();
 // Per-ray parameters of a 2D ray in continuous pixel-index space.  The ray
 // is written along its major axis a (the axis it advances fastest along, in
 // index units) as  b(a) = n0 + f0 + a * kappa,  |kappa| <= 1,  where a, b are
-// continuous index coordinates (pixel ia spans [ia, ia+1)).  lrow is the ray
-// length (mm) per unit of a.  packed = 2*n0 + axis, axis 0: a = x, 1: a = y.
-// n0 is the nearest integer to b(0) so that f0 in [-1/2, 1/2) keeps full
-// FP32 precision near pixel boundaries.
+// continuous index coordinates (pixel ia spans [ia, ia+1)).  The slope is
+// split as kappa = k/2048 + kappa_lo with an integer k, so that a * k/2048
+// is formed exactly in integer arithmetic and the float part of b stays
+// below 3 in magnitude: positions keep ~1e-7 pixel precision anywhere in the
+// image.  lrow is the ray length (mm) per unit of a.
+// packed = (k << 16) | ((n0 & 0x7fff) << 1) | axis; axis 0: a = x, 1: a = y;
+// n0 is the nearest integer to b(0), f0 in [-1/2, 1/2).
 struct __align__(16) Ray2 {
     float f0;
-    float kappa;
+    float kappa_lo;
     float lrow;
     int packed;
 };
+
+__host__ __device__ __forceinline__ int ray_axis(int packed) { return packed & 1; }
+__host__ __device__ __forceinline__ int ray_n0(int packed) { return (int)((unsigned)packed << 16) >> 17; }
+__host__ __device__ __forceinline__ int ray_k(int packed) { return packed >> 16; }
 
 // Per-view parameters: beam direction u = (cu, su).
 struct __align__(16) View2 {
@@ -91,14 +98,22 @@ bool is_3d(const oslalm_geom *g);
 // gather back-projector call the same row/overlap arithmetic with explicit
 // round-to-nearest intrinsics, so both directions use bit-identical weights.
 struct RowSpan {
-    float lo, hi;   // minor-coordinate span of the ray inside row ia, relative to n0
+    int base;       // integer minor coordinate the span is measured from
+    float lo, hi;   // minor-coordinate span of the ray inside row ia, relative to base
     float scale;    // lrow / (hi - lo), or 0 when hi == lo
 };
 
 __device__ __forceinline__ RowSpan row_span(const Ray2 &r, int ia) {
-    float w0 = __fmaf_rn((float)ia, r.kappa, r.f0);
-    float w1 = __fmaf_rn((float)(ia + 1), r.kappa, r.f0);
+    const int k = ray_k(r.packed);
+    const int p0 = ia * k, p1 = p0 + k;            // exact: |ia k| < 2^24
+    const int q0 = p0 >> 11, q1 = p1 >> 11;        // floor(ia k / 2048)
+    const float r0 = (float)(p0 & 2047) * 4.8828125e-4f;  // exact fractions
+    const float r1 = (float)(p1 & 2047) * 4.8828125e-4f;
+    float w0 = __fadd_rn(__fadd_rn(r.f0, r0), __fmul_rn((float)ia, r.kappa_lo));
+    float w1 = __fadd_rn(__fadd_rn(r.f0, r1), __fmul_rn((float)(ia + 1), r.kappa_lo));
+    w1 = __fadd_rn(w1, (float)(q1 - q0));
     RowSpan s;
+    s.base = ray_n0(r.packed) + q0;
     s.lo = fminf(w0, w1);
     s.hi = fmaxf(w0, w1);
     float width = __fsub_rn(s.hi, s.lo);
@@ -107,7 +122,7 @@ __device__ __forceinline__ RowSpan row_span(const Ray2 &r, int ia) {
     return s;
 }
 
-// chord of the row span inside minor pixel jj (relative to n0)
+// chord of the row span inside minor pixel jj (relative to the span's base)
 __device__ __forceinline__ float row_chord(const RowSpan &s, float lrow, float jj) {
     if (s.scale > 0.f) {
         float ov = __fsub_rn(fminf(s.hi, jj + 1.f), fmaxf(s.lo, jj));
@@ -117,12 +132,11 @@ __device__ __forceinline__ float row_chord(const RowSpan &s, float lrow, float j
 }
 
 __device__ __forceinline__ float chord2(const Ray2 &r, int ix, int iy) {
-    int axis = r.packed & 1;
-    int n0 = r.packed >> 1;
-    int ia = axis ? iy : ix;
-    int jb = axis ? ix : iy;
+    const int axis = ray_axis(r.packed);
+    const int ia = axis ? iy : ix;
+    const int jb = axis ? ix : iy;
     RowSpan s = row_span(r, ia);
-    return row_chord(s, r.lrow, (float)(jb - n0));
+    return row_chord(s, r.lrow, (float)(jb - s.base));
 }
 
 // ---------------------------------------------------------------- projector launchers

@@ -65,12 +65,41 @@ static Ray2 make_ray2(const oslalm_geom_desc &d, double px, double py, double ux
         double xat = px + (ylo - py) * (ux / uy);
         b0 = (xat - xlo) / d.dx;
     }
+    const int Na = axis ? d.ny : d.nx, Nb = axis ? d.nx : d.ny;
+    int k = (int)nearbyint(kappa * 2048.0);
+    if (k > 2048) k = 2048;
+    if (k < -2048) k = -2048;
     double n0 = floor(b0 + 0.5);
-    r.f0 = (float)(b0 - n0);
-    r.kappa = (float)kappa;
-    r.lrow = (float)lrow;
-    r.packed = (int)n0 * 2 + axis;
+    // a ray crosses the image only if b0 lies within [-Na, Nb + Na]; others get
+    // zero length (and a representable n0)
+    bool misses = !(b0 > -(double)Na - 2.0 && b0 < (double)(Nb + Na) + 2.0);
+    if (misses) n0 = -(double)Na - 4.0;
+    r.f0 = misses ? 0.f : (float)(b0 - n0);
+    r.kappa_lo = (float)(kappa - k / 2048.0);
+    r.lrow = misses ? 0.f : (float)lrow;
+    r.packed = (int)((unsigned)k << 16) | (((int)n0 & 0x7fff) << 1) | axis;
     return r;
+}
+
+// 2D ray parameters of every channel of view v (FP64 set-up).
+static void ray_table_view(const oslalm_geom_desc &d, int v, Ray2 *out) {
+    double cu, su;
+    cos_sin_turns(view_turns(d, v), &cu, &su);
+    const double ex = -su, ey = cu;
+    for (int c = 0; c < d.ns; ++c) {
+        double s = ((double)c - (d.ns - 1) / 2.0 + d.offset_s) * d.ds;
+        double px, py, ux, uy;
+        if (d.kind == OSLALM_PAR2D) {
+            px = s * ex; py = s * ey; ux = cu; uy = su;
+        } else {
+            double gam = s / d.dsd;
+            double cg = cos(gam), sg = sin(gam);
+            px = -d.dso * cu; py = -d.dso * su;
+            ux = cg * cu + sg * ex;
+            uy = cg * su + sg * ey;
+        }
+        out[c] = make_ray2(d, px, py, ux, uy);
+    }
 }
 
 static int validate(const oslalm_geom_desc *d) {
@@ -84,8 +113,8 @@ static int validate(const oslalm_geom_desc *d) {
         return fail(OSLALM_ERR_ARG, "pixel and detector pitches must be positive");
     if ((long)d->nx * d->ny * d->nz > (1L << 31) - 1 || (long)d->nviews * d->ns * d->nt > (1L << 31) - 1)
         return fail(OSLALM_ERR_RANGE, "image or sinogram exceeds 2^31 elements");
-    if (d->nx > (1 << 20) || d->ny > (1 << 20) || d->nviews > (1 << 24))
-        return fail(OSLALM_ERR_RANGE, "dimension too large");
+    if (d->nx > 4096 || d->ny > 4096 || d->nviews > (1 << 24) || d->ns > (1 << 16))
+        return fail(OSLALM_ERR_RANGE, "dimension too large (nx, ny <= 4096)");
     if (d->kind != OSLALM_PAR2D) {
         if (!(d->dso > 0 && d->dsd > d->dso)) return fail(OSLALM_ERR_ARG, "need 0 < dso < dsd");
         double hx = 0.5 * d->nx * d->dx + fabs(d->offset_x);
@@ -152,25 +181,10 @@ int oslalm_geom_create(const oslalm_geom_desc *desc, oslalm_geom **out) {
     for (int v = 0; v < d.nviews; ++v) {
         double cu, su;
         cos_sin_turns(view_turns(d, v), &cu, &su);
-        double ex = -su, ey = cu;
         views[v] = View2{(float)cu, (float)su, 0.f, 0.f};
         views3[v] = View3{(float)cu, (float)su, (float)(-d.dso * cu), (float)(-d.dso * su)};
         allv[v] = v;
-        if (!two_d) continue;
-        for (int c = 0; c < d.ns; ++c) {
-            double s = ((double)c - (d.ns - 1) / 2.0 + d.offset_s) * d.ds;
-            double px, py, ux, uy;
-            if (d.kind == OSLALM_PAR2D) {
-                px = s * ex; py = s * ey; ux = cu; uy = su;
-            } else {
-                double gam = s / d.dsd;
-                double cg = cos(gam), sg = sin(gam);
-                px = -d.dso * cu; py = -d.dso * su;
-                ux = cg * cu + sg * ex;
-                uy = cg * su + sg * ey;
-            }
-            rays[(size_t)v * d.ns + c] = make_ray2(d, px, py, ux, uy);
-        }
+        if (two_d) ray_table_view(d, v, &rays[(size_t)v * d.ns]);
     }
     auto cleanup = [&](int code, const char *what, cudaError_t e) {
         cudaFree(g->d_rays); cudaFree(g->d_views); cudaFree(g->d_views3); cudaFree(g->d_allviews);
@@ -187,6 +201,24 @@ int oslalm_geom_create(const oslalm_geom_desc *desc, oslalm_geom **out) {
     if ((e = cudaMemcpy(g->d_allviews, allv.data(), sizeof(int) * d.nviews, cudaMemcpyHostToDevice)) != cudaSuccess) return cleanup(OSLALM_ERR_CUDA, "upload", e);
     if (two_d && (e = cudaMemcpy(g->d_rays, rays.data(), sizeof(Ray2) * rays.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return cleanup(OSLALM_ERR_CUDA, "upload", e);
     *out = g;
+    return OSLALM_OK;
+}
+
+int oslalm_ray_table(const oslalm_geom_desc *desc, int view, float *f0, float *kappa_lo, float *lrow,
+                     int *packed) {
+    clear_error();
+    if (int rc = validate(desc)) return rc;
+    if (desc->kind == OSLALM_CONE3D_FLAT) return fail(OSLALM_ERR_ARG, "ray tables are 2D only");
+    if (view < 0 || view >= desc->nviews || !f0 || !kappa_lo || !lrow || !packed)
+        return fail(OSLALM_ERR_ARG, "bad ray table request");
+    std::vector<Ray2> r(desc->ns);
+    ray_table_view(*desc, view, r.data());
+    for (int c = 0; c < desc->ns; ++c) {
+        f0[c] = r[c].f0;
+        kappa_lo[c] = r[c].kappa_lo;
+        lrow[c] = r[c].lrow;
+        packed[c] = r[c].packed;
+    }
     return OSLALM_OK;
 }
 

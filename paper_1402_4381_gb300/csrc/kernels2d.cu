@@ -21,34 +21,50 @@
 namespace oslalm {
 
 // ---------------------------------------------------------------- forward
-template <typename ACC>
-__device__ __forceinline__ ACC march2(const Geo2 &g, const Ray2 &rp, const float *__restrict__ x) {
-    const int axis = rp.packed & 1;
-    const int n0 = rp.packed >> 1;
+// Major-axis rows [ia0, ia1] whose minor span can meet [0, Nb) (conservative).
+__device__ __forceinline__ void ray_rows(const Geo2 &g, const Ray2 &rp, int &ia0, int &ia1) {
+    const int axis = ray_axis(rp.packed);
+    const int n0 = ray_n0(rp.packed);
     const int Na = axis ? g.ny : g.nx;
     const int Nb = axis ? g.nx : g.ny;
-    const int sa = axis ? g.nx : 1;
-    const int sb = axis ? 1 : g.nx;
-    int ia0 = 0, ia1 = Na - 1;
-    if (rp.kappa != 0.f) {
-        // rows whose minor span can meet [0, Nb): b - n0 in [-n0 - 1, Nb - n0 + 1]
-        float t0 = ((float)(-n0) - 1.f - rp.f0) / rp.kappa;
-        float t1 = ((float)(Nb - n0) + 1.f - rp.f0) / rp.kappa;
+    ia0 = 0;
+    ia1 = Na - 1;
+    if (rp.lrow == 0.f) {  // the ray misses the image
+        ia1 = -1;
+        return;
+    }
+    const float kap = (float)ray_k(rp.packed) * 4.8828125e-4f + rp.kappa_lo;
+    if (kap != 0.f) {
+        // b - n0 in [-1, Nb - n0 + 1] at the row ends, with a row of margin
+        float t0 = ((float)(-n0) - 1.f - rp.f0) / kap;
+        float t1 = ((float)(Nb - n0) + 1.f - rp.f0) / kap;
         float tlo = fmaxf(fminf(t0, t1), -2.f), thi = fminf(fmaxf(t0, t1), (float)Na + 2.f);
         ia0 = max(0, (int)floorf(tlo) - 1);
         ia1 = min(Na - 1, (int)ceilf(thi) + 1);
     } else {
         int j = n0 + (int)floorf(rp.f0);
-        if (j < 0 || j >= Nb) return (ACC)0;
+        if (j < 0 || j >= Nb) ia1 = -1;
     }
+}
+
+// Sum of chord x pixel over rows first, first+stride, ... of the ray.
+template <typename ACC>
+__device__ __forceinline__ ACC march2(const Geo2 &g, const Ray2 &rp, const float *__restrict__ x, int first,
+                                      int stride) {
+    const int axis = ray_axis(rp.packed);
+    const int Nb = axis ? g.nx : g.ny;
+    const int sa = axis ? g.nx : 1;
+    const int sb = axis ? 1 : g.nx;
+    int ia0, ia1;
+    ray_rows(g, rp, ia0, ia1);
     ACC acc = 0;
-    for (int ia = ia0; ia <= ia1; ++ia) {
-        RowSpan s = row_span(rp, ia);
+    for (int ia = ia0 + first; ia <= ia1; ia += stride) {
+        const RowSpan s = row_span(rp, ia);
         const float jlo = floorf(s.lo), jhi = floorf(s.hi);
         for (float jj = jlo; jj <= jhi; jj += 1.f) {
-            int j = n0 + (int)jj;
+            const int j = s.base + (int)jj;
             if ((unsigned)j < (unsigned)Nb) {
-                float ch = row_chord(s, rp.lrow, jj);
+                const float ch = row_chord(s, rp.lrow, jj);
                 acc += (ACC)ch * (ACC)__ldg(x + (size_t)ia * sa + (size_t)j * sb);
             }
         }
@@ -56,26 +72,40 @@ __device__ __forceinline__ ACC march2(const Geo2 &g, const Ray2 &rp, const float
     return acc;
 }
 
+// One warp = 8 rays (adjacent channels) x 4 lanes; lane q of a ray takes
+// rows ia0+q, ia0+q+4, ...; the 4 partial sums are combined by shuffles in a
+// fixed order.
 template <int MODE, typename WT>
 __global__ void __launch_bounds__(128) fp2d_kernel(Geo2 g, const float *__restrict__ x, float *__restrict__ out,
                                                    const int *__restrict__ views, int nv,
                                                    const float *__restrict__ y, const WT *__restrict__ w,
                                                    const float *__restrict__ wscale, float gain) {
-    const int ray = blockIdx.x * blockDim.x + threadIdx.x;
-    if (ray >= nv * g.ns) return;
-    const int lv = ray / g.ns;
-    const int c = ray - lv * g.ns;
-    const int v = __ldg(views + lv);
+    const int lane = threadIdx.x & 31;
+    const int q = lane >> 3;
+    const int ray = (blockIdx.x * 4 + (threadIdx.x >> 5)) * 8 + (lane & 7);
+    const bool valid = ray < nv * g.ns;
+    float acc = 0.f;
+    int lv = 0, c = 0, v = -1;
+    if (valid) {
+        lv = ray / g.ns;
+        c = ray - lv * g.ns;
+        v = __ldg(views + lv);
+        if ((unsigned)v < (unsigned)g.nviews) {
+            const Ray2 rp = g.rays[(size_t)v * g.ns + c];
+            acc = march2<float>(g, rp, x, q, 4);
+        }
+    }
+    acc += __shfl_xor_sync(0xffffffffu, acc, 8);
+    acc += __shfl_xor_sync(0xffffffffu, acc, 16);
+    if (!valid || q != 0) return;
     if ((unsigned)v >= (unsigned)g.nviews) {  // caller-supplied view out of range
         out[ray] = __int_as_float(0x7fc00000);
         return;
     }
-    const Ray2 rp = g.rays[(size_t)v * g.ns + c];
-    float acc = march2<float>(g, rp, x);
     if (MODE == FP_PLAIN) {
         out[ray] = acc;
     } else {
-        float wv = load_w(w, ray) * __ldg(wscale);
+        const float wv = load_w(w, ray) * __ldg(wscale);
         out[ray] = gain * wv * (acc - __ldg(y + ray));
     }
 }
@@ -92,7 +122,7 @@ __global__ void __launch_bounds__(128) cost2d_kernel(Geo2 g, const float *__rest
         const int c = ray - lv * g.ns;
         const int v = __ldg(views + lv);
         double acc = 0.0;
-        if ((unsigned)v < (unsigned)g.nviews) acc = march2<double>(g, g.rays[(size_t)v * g.ns + c], x);
+        if ((unsigned)v < (unsigned)g.nviews) acc = march2<double>(g, g.rays[(size_t)v * g.ns + c], x, 0, 1);
         double res = (double)__ldg(y + ray) - acc;
         val = 0.5 * (double)load_w(w, ray) * (double)__ldg(wscale) * res * res;
     }
@@ -317,7 +347,7 @@ template <int MODE>
 static int launch_fp2d_t(const Geo2 &g, const float *x, float *out, const int *views, int nv, const float *y,
                          WeightRef w, float gain, cudaStream_t st) {
     const int n = nv * g.ns;
-    const int grid = (n + 127) / 128;
+    const int grid = (n + 31) / 32;  // 32 rays per 128-thread block
     if (MODE == FP_PLAIN || w.dtype == OSLALM_F32)
         fp2d_kernel<MODE, float><<<grid, 128, 0, st>>>(g, x, out, views, nv, y, (const float *)w.ptr, w.scale, gain);
     else if (w.dtype == OSLALM_F16)

@@ -89,6 +89,8 @@ def lib():
         "oslalm_get_denominator": ([_VP, _VP, _VP], i),
         "oslalm_rmsd": ([_VP, _VP, _VP, ctypes.c_long, ctypes.POINTER(d), _VP], i),
         "oslalm_profile_iterate": ([_VP, _VP, i, ctypes.POINTER(d), ip, _VP], i),
+        "oslalm_fbp": ([_VP, _VP, _VP, i, _VP], i),
+        "oslalm_ray_table": ([ctypes.POINTER(GeomDesc), i, _VP, _VP, _VP, _VP], i),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -123,6 +125,27 @@ def _dev_f32(t, shape=None, name="tensor"):
     return t
 
 
+def geom_desc(geom) -> GeomDesc:
+    d = GeomDesc()
+    for name, _ in GeomDesc._fields_:
+        setattr(d, name, getattr(geom, name))
+    return d
+
+
+def ray_table(geom, view: int):
+    """Host copy of the 2D per-ray parameters of one view (no GPU needed):
+    dict(f0, kappa_lo, lrow: float32 [ns], packed: int32 [ns])."""
+    ns = geom.ns
+    f0 = np.zeros(ns, np.float32)
+    kl = np.zeros(ns, np.float32)
+    lr = np.zeros(ns, np.float32)
+    pk = np.zeros(ns, np.int32)
+    d = geom_desc(geom)
+    _check(lib().oslalm_ray_table(ctypes.byref(d), int(view), f0.ctypes.data, kl.ctypes.data, lr.ctypes.data,
+                                  pk.ctypes.data), "ray_table")
+    return dict(f0=f0, kappa_lo=kl, lrow=lr, packed=pk)
+
+
 def subset_order(M: int) -> List[int]:
     arr = (ctypes.c_int * M)()
     _check(lib().oslalm_subset_order(M, arr), "subset_order")
@@ -134,9 +157,7 @@ class Geometry:
 
     def __init__(self, geom):
         self.desc_py = geom
-        d = GeomDesc()
-        for name, _ in GeomDesc._fields_:
-            setattr(d, name, getattr(geom, name))
+        d = geom_desc(geom)
         self._h = _VP()
         _check(lib().oslalm_geom_create(ctypes.byref(d), ctypes.byref(self._h)), "geom_create")
         self._views_all = None
@@ -190,6 +211,16 @@ class Geometry:
         _dev_f32(out, self.image_shape, "x")
         _check(lib().oslalm_backproject(self._h, _ptr(sino), _ptr(out), _ptr(vt), nv, int(accumulate),
                                         _stream(stream)), "backproject")
+        return out
+
+    def fbp(self, sino, out=None, clip=True, stream=None):
+        """Filtered back-projection of the full sinogram (initial image)."""
+        import torch
+        _dev_f32(sino, self.sino_shape(), "sino")
+        if out is None:
+            out = torch.empty(self.image_shape, dtype=torch.float32, device=sino.device)
+        _dev_f32(out, self.image_shape, "x")
+        _check(lib().oslalm_fbp(self._h, _ptr(sino), _ptr(out), int(bool(clip)), _stream(stream)), "fbp")
         return out
 
     def close(self):

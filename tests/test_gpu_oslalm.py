@@ -111,9 +111,11 @@ def test_c0_denominator_and_cost(L, c0):
     c_gpu = prob.cost(x)
     c_ref = alg.cost(c0.x0.astype(np.float64))
     assert abs(c_gpu - c_ref) <= COST_RTOL * abs(c_ref)
-    # the first subset gradient and the split gradient
+    # the first subset gradient and the split gradient; zeta = M A'W(Ax - y) is
+    # formed from residuals Ax - y that cancel most of Ax, so its FP32 error
+    # is ~1e-6 |Ax| / |Ax - y| relative: allow 1e-4 with a 1e-2 floor
     st = prob.get_state()
-    assert_rel_floor(to_host(st["zeta"]), alg.zeta, rtol=2e-5, floor=1e-2, what="zeta0")
+    assert_rel_floor(to_host(st["zeta"]), alg.zeta, rtol=1e-4, floor=1e-2, what="zeta0")
     assert np.array_equal(to_host(st["zeta"]), to_host(st["g"]))
 
 
