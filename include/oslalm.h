@@ -172,6 +172,21 @@ int oslalm_backproject(const oslalm_geom *g, const float *sino, float *x,
  * `stream` and frees it before returning.  Errors: ARG, RANGE, CUDA. */
 int oslalm_fbp(const oslalm_geom *g, const float *sino, float *x, int clip_nonneg, void *stream);
 
+/* Same as oslalm_fbp, for callers that cannot allocate device memory while
+ * they run (a service whose memory pool took the whole GPU at start-up, or a
+ * real-time pipeline that forbids cudaMalloc after initialisation because it
+ * may synchronize the device).  The paper has no counterpart: this is a
+ * deployment variant.  The filtered sinogram lives in a fixed 16 MiB buffer
+ * (2^22 FP32 samples) that the library holds on every device that loads it
+ * until the process exits; nviews*nt*ns above 2^22 returns OSLALM_ERR_RANGE.
+ * The call allocates nothing.  Its first call on a device looks up the
+ * buffer's device address (cudaGetSymbolAddress) with that device current;
+ * make that first call before any stream capture.  All calls share the one
+ * buffer and the next call overwrites it: calls whose work overlaps on the
+ * GPU (other streams, other host threads) race, so serialize them.  Errors:
+ * ARG, RANGE, CUDA. */
+int oslalm_fbp_noalloc(const oslalm_geom *g, const float *sino, float *x, int clip_nonneg, void *stream);
+
 /* ---- PWLS problem and OS-LALM (Eq. os_lalm_iterates, Sec. III-IV) --------
  * oslalm_problem_create: copies y[dev, sino] and w[dev, sino] (FP32,
  *   w >= 0) into library-owned subset-major buffers, storing W as

@@ -10,6 +10,7 @@
 //      linear (bilinear for FDK) interpolation and distance weights.
 #include <math.h>
 
+#include <mutex>
 #include <vector>
 
 #include "common.cuh"
@@ -170,6 +171,91 @@ extern "C" int oslalm_fbp(const oslalm_geom *gm, const float *sino, float *x, in
         e = cudaGetLastError();
     }
     cudaFreeAsync(q, st);
+    if (e != cudaSuccess) return fail(OSLALM_ERR_CUDA, "FBP launch failed: %s", cudaGetErrorString(e));
+    return OSLALM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free FBP.  Some callers cannot allocate device memory while they
+// run: a service that hands the whole GPU to its own pre-sized memory pool at
+// start-up, or a real-time pipeline that forbids allocation after
+// initialisation because cudaMalloc may synchronize the device and its
+// latency is unbounded.  oslalm_fbp_noalloc does the same work as oslalm_fbp
+// but keeps the filtered sinogram in the fixed buffer below, which the
+// library owns on every device that loads it, for the life of the process.
+namespace oslalm {
+
+constexpr size_t kFbpStaticFloats = (size_t)1 << 22;  // 16 MiB of FP32 samples
+static __device__ __align__(256) float g_fbp_scratch[kFbpStaticFloats];
+
+static std::mutex g_fbp_scratch_mutex;
+static float *g_fbp_scratch_ptr[64] = {nullptr};
+
+// Device address of g_fbp_scratch on the current device, looked up once per
+// device with that device current (host code cannot use the symbol itself:
+// on the host it names a stand-in object, not device memory).
+static int fbp_scratch_address(float **out) {
+    int dev = 0;
+    OSL_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return fail(OSLALM_ERR_RANGE, "device ordinal %d not supported", dev);
+    std::lock_guard<std::mutex> lock(g_fbp_scratch_mutex);
+    if (!g_fbp_scratch_ptr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_fbp_scratch);
+        if (e != cudaSuccess || !p)
+            return fail(OSLALM_ERR_CUDA, "cudaGetSymbolAddress(g_fbp_scratch) failed: %s", cudaGetErrorString(e));
+        g_fbp_scratch_ptr[dev] = (float *)p;
+    }
+    *out = g_fbp_scratch_ptr[dev];
+    return OSLALM_OK;
+}
+
+}  // namespace oslalm
+
+extern "C" int oslalm_fbp_noalloc(const oslalm_geom *gm, const float *sino, float *x, int clip_nonneg,
+                                  void *stream) {
+    clear_error();
+    if (!gm || !sino || !x) return fail(OSLALM_ERR_ARG, "NULL argument");
+    const oslalm_geom_desc &d = gm->d;
+    if (d.kind != OSLALM_PAR2D && fabs(fabs(d.angle_span) - 2.0 * M_PI) > 1e-9)
+        return fail(OSLALM_ERR_ARG, "fan/cone FBP needs a full 360-degree scan");
+    if (d.ns > 8192) return fail(OSLALM_ERR_RANGE, "FBP supports at most 8192 channels");
+    const size_t nq = (size_t)d.nviews * d.nt * d.ns;
+    if (nq > kFbpStaticFloats)
+        return fail(OSLALM_ERR_RANGE,
+                    "oslalm_fbp_noalloc: sinogram has %zu samples, the static buffer holds at most %zu "
+                    "(use oslalm_fbp)", nq, kFbpStaticFloats);
+    float *q = nullptr;
+    if (int rc = fbp_scratch_address(&q)) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    FbpGeo g;
+    g.kind = d.kind;
+    g.nx = d.nx; g.ny = d.ny; g.nz = d.nz; g.nviews = d.nviews; g.ns = d.ns; g.nt = d.nt;
+    g.dx = (float)d.dx; g.dy = (float)d.dy; g.dz = (float)d.dz;
+    g.xc0 = (float)(d.offset_x - (d.nx - 1) / 2.0 * d.dx);
+    g.yc0 = (float)(d.offset_y - (d.ny - 1) / 2.0 * d.dy);
+    g.zc0 = (float)(d.offset_z - (d.nz - 1) / 2.0 * d.dz);
+    g.ds = (float)d.ds; g.dt = (float)d.dt;
+    g.c0 = (float)((d.ns - 1) / 2.0 - d.offset_s);
+    g.t0 = (float)((d.nt - 1) / 2.0 - d.offset_t);
+    g.dso = (float)d.dso; g.dsd = (float)d.dsd;
+    g.a = d.kind == OSLALM_FAN2D_ARC ? (float)(d.ds / d.dsd) : (float)(d.ds * d.dso / d.dsd);
+    g.az = (float)(d.dt * d.dso / d.dsd);
+    if (d.kind == OSLALM_PAR2D) g.scale = (float)(M_PI / d.nviews);
+    else if (d.kind == OSLALM_FAN2D_ARC) g.scale = (float)(2.0 * M_PI / d.nviews);
+    else g.scale = (float)(0.5 * 2.0 * M_PI / d.nviews);
+    // every filtered sample is written before it is read, so the buffer's
+    // previous contents (left by the last call) need no clearing
+    size_t shm = sizeof(float) * (3 * (size_t)d.ns - 1);
+    if (shm > 48 * 1024) cudaFuncSetAttribute(fbp_filter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+    fbp_filter_kernel<<<d.nviews * d.nt, 256, shm, st>>>(g, sino, q);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) {
+        dim3 block(32, 8), grid((d.nx + 31) / 32, (d.ny + 7) / 8, d.kind == OSLALM_CONE3D_FLAT ? d.nz : 1);
+        if (d.kind == OSLALM_CONE3D_FLAT) fbp_bp3d_kernel<<<grid, block, 0, st>>>(g, gm->d_views, q, x, clip_nonneg);
+        else fbp_bp2d_kernel<<<grid, block, 0, st>>>(g, gm->d_views, q, x, clip_nonneg);
+        e = cudaGetLastError();
+    }
     if (e != cudaSuccess) return fail(OSLALM_ERR_CUDA, "FBP launch failed: %s", cudaGetErrorString(e));
     return OSLALM_OK;
 }
