@@ -42,6 +42,9 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-time-to-hu", action="store_true")
+    ap.add_argument("--workload", default="fan", choices=["fan", "cone", "parallel"],
+                    help="fan: the 512^2 fan-beam scan (default, the headline); cone / parallel: the "
+                         "512x512x128 cone-beam and 128^2 parallel-beam scans")
     return ap.parse_args()
 
 
@@ -97,40 +100,55 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def intersections_per_subset(geom, M):
-    """Number of (ray, pixel) pairs with a non-zero length, per subset on
-    average: for each ray clipped to the image box, the pixels it crosses are
-    1 + (column crossings) + (row crossings)."""
+def intersections_per_subset(geom, M, max_views=24):
+    """Number of (ray, pixel/voxel) pairs with a non-zero length, per subset
+    on average, counted in closed form per ray: a ray clipped to the image box
+    crosses 1 + (number of grid planes between its entry and exit points)
+    cells.  Counted on up to max_views evenly spaced views and scaled."""
     from paper_1402_4381_gb300 import synth
-    org, d = synth.rays(geom)
-    org, d = org[..., :2].reshape(-1, 2), d[..., :2].reshape(-1, 2)
-    lo = np.array([-geom.nx * geom.dx / 2, -geom.ny * geom.dy / 2])
+    views = np.linspace(0, geom.nviews - 1, min(max_views, geom.nviews)).round().astype(int)
+    org, d = synth.rays(geom, views)
+    three = geom.kind == synth.CONE3D_FLAT
+    nd = 3 if three else 2
+    org, d = org[..., :nd].reshape(-1, nd), d[..., :nd].reshape(-1, nd)
+    size = [geom.nx * geom.dx, geom.ny * geom.dy, geom.nz * geom.dz][:nd]
+    lo = -np.array(size) / 2
     hi = -lo
     with np.errstate(divide="ignore", invalid="ignore"):
         t0 = np.full(len(org), -np.inf)
         t1 = np.full(len(org), np.inf)
-        for k in range(2):
+        for k in range(nd):
             a = (lo[k] - org[:, k]) / d[:, k]
             b = (hi[k] - org[:, k]) / d[:, k]
-            t0 = np.maximum(t0, np.minimum(a, b))
-            t1 = np.minimum(t1, np.maximum(a, b))
+            t0 = np.maximum(t0, np.where(d[:, k] != 0, np.minimum(a, b), -np.inf))
+            t1 = np.minimum(t1, np.where(d[:, k] != 0, np.maximum(a, b), np.inf))
     ok = t1 > t0
     pe = org[ok] + t0[ok, None] * d[ok]
     px = org[ok] + t1[ok, None] * d[ok]
-    pix = np.array([geom.dx, geom.dy])
+    pix = np.array([geom.dx, geom.dy, geom.dz][:nd])
     ie = np.floor((np.clip(pe, lo, hi - 1e-9) - lo) / pix)
     ix = np.floor((np.clip(px, lo, hi - 1e-9) - lo) / pix)
     n = np.sum(np.abs(ix - ie), axis=1) + 1
-    return float(n.sum()) / M
+    return float(n.sum()) * geom.nviews / len(views) / M
 
 
 def roi_mask(geom):
-    """Field-of-view disk (pixels whose centre the fan of rays covers)."""
+    """Field of view: pixels inside the disk every view covers; for the cone
+    beam also voxels that project inside the detector rows from every view."""
     ix = (np.arange(geom.nx) - (geom.nx - 1) / 2.0) * geom.dx
     iy = (np.arange(geom.ny) - (geom.ny - 1) / 2.0) * geom.dy
     Y, X = np.meshgrid(iy, ix, indexing="ij")
-    R = geom.dso * math.sin(geom.ns * geom.ds / 2.0 / geom.dsd)
-    return (np.sqrt(X * X + Y * Y) <= R)[None]
+    r = np.sqrt(X * X + Y * Y)
+    if geom.kind == 0:
+        R = geom.ns * geom.ds / 2.0
+    else:
+        R = geom.dso * math.sin(geom.ns * geom.ds / 2.0 / geom.dsd)
+    m2 = (r <= R)[None]
+    if geom.kind != 2:
+        return m2
+    iz = (np.arange(geom.nz) - (geom.nz - 1) / 2.0) * geom.dz
+    mag = geom.dsd / np.maximum(geom.dso - r, 1e-9)
+    return m2 & (np.abs(iz)[:, None, None] * mag[None] <= geom.nt * geom.dt / 2.0)
 
 
 def peaks():
@@ -167,7 +185,7 @@ def run_reference(args):
     if rank != 0:
         return 0
     from paper_1402_4381_gb300 import workloads as W
-    wl = W.c1_fan()
+    wl = {"fan": W.c1_fan, "cone": W.c2_cone, "parallel": W.c0_parallel}[args.workload]()
     scan = wl.make_scan()
     from oracle import fbp as ofbp
     x0 = np.maximum(ofbp.fbp(wl.geom, scan["y"].astype(np.float64)), 0.0)
@@ -200,7 +218,7 @@ def run_ours(args):
         torch.cuda.set_device(0)
     from paper_1402_4381_gb300 import oslalm, workloads as W
 
-    wl = W.c1_fan()
+    wl = {"fan": W.c1_fan, "cone": W.c2_cone, "parallel": W.c0_parallel}[args.workload]()
     if world > 1:  # independent replicas: a different noise realisation per rank
         wl.noise_seed += 1000 * rank
     g = wl.geom
@@ -293,7 +311,7 @@ def run_ours(args):
     # ---- per-kernel device time (CUDA events around each launch kind)
     x.copy_(x0)
     prob.init(x)
-    prof = prob.profile_iterate(x, 4)
+    prof = prob.profile_iterate(x, 4 if g.kind != 2 else 1)
     nl = prof["launches"][0]
     per = {"update": prof["update"] / nl, "forward": prof["forward"] / nl, "backproject": prof["backproject"] / nl}
     dom = max(per, key=per.get)
@@ -310,34 +328,34 @@ def run_ours(args):
                 "work_per_launch": f"{inter:.4g} intersections x 3 FP32 ops",
                 "peak_basis": f"152 SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz (median SM clock under load)"}
     else:
-        bytes_px = 4 + 4 + 4 + 2 + 4  # x, zeta, g read; D (fp16) read; x+ write
-        traffic = bytes_px * g.nx * g.ny
+        bytes_px = 4 + 4 + 4 + (4 if wl.d_dtype == "f32" else 2) + 4  # x, zeta, g, D read; x+ write
+        traffic = bytes_px * g.nx * g.ny * g.nz
         achieved = traffic / (per[dom] / 1000.0)
         hbm = (pk or {}).get("hbm_gbs", 6800.0) * 1e9
-        roof = {"kernel": "update2d_kernel", "bound": "hbm", "achieved": achieved / 1e9, "peak": hbm / 1e9,
+        roof = {"kernel": f"update{dim}_kernel", "bound": "hbm", "achieved": achieved / 1e9, "peak": hbm / 1e9,
                 "unit": "GB/s", "frac": achieved / hbm, "traffic": None}
     roof["per_kernel_ms"] = {k: round(v, 5) for k, v in per.items()}
 
     # ---- time to 1 HU against a converged image (M = 1 continuation, long run)
     ttu = None
-    if not args.no_time_to_hu:
+    if not args.no_time_to_hu and g.kind != 2:
         ttu = time_to_hu(torch, oslalm, wl, geom, y, w, x0, mask_np, dev, stream)
         ttu["fbp_setup_ms"] = fbp_ms
 
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "metric": METRIC if args.workload == "fan" else f"A/A' subset-iters/s (OS-LALM, {wl.name})", "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": wl.name, "image": [g.nx, g.ny], "views": g.nviews, "channels": g.ns, "M": wl.M,
                    "iterations_per_step": wl.n_iter, "storage": {"W": wl.w_dtype, "D": wl.d_dtype},
                    "parallelism": f"replicas{world}", "l2": "flushed between timed steps (256 MB write)"},
-        "gpu_launches": args.steps * (wl.n_iter * wl.M * 3 + 2),
+        "gpu_launches": args.steps * (wl.n_iter * wl.M * 3 + 3),
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "roofline": roof, "clocks": clocks,
     }
     if ttu:
         line["time_to_1hu"] = ttu
-    if rank == 0 and not args.no_cpu_baseline:
+    if rank == 0 and not args.no_cpu_baseline and g.kind != 2:
         times = oracle_sample(wl, scan, x0_np, 5)
         t = sum(times[1:])
         line["cpu_baseline"] = {"value": len(times[1:]) / t, "unit": UNIT, "cores": 1, "kind": "oracle",

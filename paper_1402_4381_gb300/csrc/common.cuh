@@ -65,6 +65,36 @@ struct __align__(16) View3 {
     float srcx, srcy;  // source position (z = 0)
 };
 
+// Cone beam, flat detector: all rays of channel c in view v lie in the plane
+// through the source and detector column c, so every detector row shares the
+// transaxial line xy (a Ray2).  The height law of the row-t ray in voxel
+// units above the volume's bottom face is
+//     zb(a) = u (Z0 + a Z1) + oz,   u = 2 (t - t0) (an integer),
+// Z0 = alpha0 dt / (2 dz), Z1 = alpha1 dt / (2 dz) with alpha = alpha0 +
+// a alpha1 the fraction of the transaxial way from the source to the detector
+// at major index a.  For FP32 precision independent of the height, Z0 is split
+// as z0h (15 significant bits, so u z0h is exact) + z0l, and Z1 / 2 as
+// kw / 2^sw (integer kw, |kw| < 512, so u (2a+1) kw is an exact int32) + w1l;
+// oz = oz_i + oz_f.  q = dt / (2 l_D) gives the 3D length per unit of a as
+// lrow sqrt(1 + (u q)^2).
+struct __align__(16) Ray3 {
+    Ray2 xy;
+    float z0h, z0l, w1l, q;
+    int kw, sw, oz_i;
+    float oz_f;
+};
+struct Geo3 {  // kernel-side cone geometry (by value)
+    int nx, ny, nz, ns, nt, nviews;
+    float dx, dy, dz, inv_dz;
+    float zlo;       // bottom face of the volume (mm)
+    float xlo, ylo;
+    float dt, t0;    // row pitch; row coordinate of t_t = 0: (nt-1)/2 - offset_t
+    int u0;          // 2 t0 (an integer): u = 2 t - u0
+    float inv_ds, c0, dso, dsd, half_diag;
+    const Ray3 *rays;    // [nviews][ns]
+    const View2 *views;  // [nviews]
+};
+
 struct Geo2 {  // kernel-side 2D geometry (by value)
     int kind, nx, ny, ns, nviews;
     float dx, dy, xlo, ylo;  // pixel size, image lower corner (mm)
@@ -81,11 +111,13 @@ struct Geo2 {  // kernel-side 2D geometry (by value)
 struct oslalm_geom {
     oslalm_geom_desc d;
     int device;
+    oslalm::Ray3 *d_rays3;    // 3D: [nviews][ns]
     oslalm::Ray2 *d_rays;     // 2D: [nviews][ns]
     oslalm::View2 *d_views;   // [nviews]
     oslalm::View3 *d_views3;  // 3D: [nviews]
     int *d_allviews;          // 0..nviews-1
     oslalm::Geo2 geo2() const;
+    oslalm::Geo3 geo3() const;
 };
 
 namespace oslalm {
@@ -94,41 +126,45 @@ bool is_3d(const oslalm_geom *g);
 
 // ---------------------------------------------------------------- chords
 // Length of a 2D ray inside pixel (ia, jb) given in the ray's (major, minor)
-// index coordinates.  The forward projector (marching along a) and the
-// gather back-projector call the same row/overlap arithmetic with explicit
-// round-to-nearest intrinsics, so both directions use bit-identical weights.
+// index coordinates.  Row ia (a in [ia, ia+1]) is entered through the ray's
+// position at the row centre, c = b(ia + 1/2), and the half-width |kappa|/2:
+// the row covers minor coordinates [c - |kappa|/2, c + |kappa|/2].  A row
+// that stays inside one pixel gives that pixel the full row length lrow; a
+// row that crosses pixel boundaries splits lrow by the overlaps.  The forward
+// projector (marching along a) and the gather back-projector call these same
+// functions, so both directions use bit-identical weights.
 struct RowSpan {
     int base;       // integer minor coordinate the span is measured from
     float lo, hi;   // minor-coordinate span of the ray inside row ia, relative to base
-    float scale;    // lrow / (hi - lo), or 0 when hi == lo
 };
+
+__device__ __forceinline__ float rcp_approx(float v) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
+    return r;
+}
 
 __device__ __forceinline__ RowSpan row_span(const Ray2 &r, int ia) {
     const int k = ray_k(r.packed);
-    const int p0 = ia * k, p1 = p0 + k;            // exact: |ia k| < 2^24
-    const int q0 = p0 >> 11, q1 = p1 >> 11;        // floor(ia k / 2048)
-    const float r0 = (float)(p0 & 2047) * 4.8828125e-4f;  // exact fractions
-    const float r1 = (float)(p1 & 2047) * 4.8828125e-4f;
-    float w0 = __fadd_rn(__fadd_rn(r.f0, r0), __fmul_rn((float)ia, r.kappa_lo));
-    float w1 = __fadd_rn(__fadd_rn(r.f0, r1), __fmul_rn((float)(ia + 1), r.kappa_lo));
-    w1 = __fadd_rn(w1, (float)(q1 - q0));
+    const int p = (2 * ia + 1) * k;                 // exact: |p| < 2^24
+    const int q = p >> 12;                          // floor((ia + 1/2) k / 2048)
+    const float fr = __fmul_rn((float)(p & 4095), 2.44140625e-4f);  // exact fraction
+    const float c = __fmaf_rn((float)ia + 0.5f, r.kappa_lo, __fadd_rn(r.f0, fr));
+    const float hw = fabsf(__fmaf_rn((float)k, 2.44140625e-4f, __fmul_rn(0.5f, r.kappa_lo)));
     RowSpan s;
-    s.base = ray_n0(r.packed) + q0;
-    s.lo = fminf(w0, w1);
-    s.hi = fmaxf(w0, w1);
-    float width = __fsub_rn(s.hi, s.lo);
-    // widths below 1e-30 (never produced by a real geometry) count as zero
-    s.scale = width > 1e-30f ? __fmul_rn(__frcp_rn(width), r.lrow) : 0.f;
+    s.base = ray_n0(r.packed) + q;
+    s.lo = __fsub_rn(c, hw);
+    s.hi = __fadd_rn(c, hw);
     return s;
 }
 
-// chord of the row span inside minor pixel jj (relative to the span's base)
+// length of the row inside minor pixel jj (relative to the span's base)
 __device__ __forceinline__ float row_chord(const RowSpan &s, float lrow, float jj) {
-    if (s.scale > 0.f) {
-        float ov = __fsub_rn(fminf(s.hi, jj + 1.f), fmaxf(s.lo, jj));
-        return ov > 0.f ? __fmul_rn(ov, s.scale) : 0.f;
-    }
-    return floorf(s.lo) == jj ? lrow : 0.f;
+    const float jl = floorf(s.lo), jh = floorf(s.hi);
+    if (jl == jh) return jj == jl ? lrow : 0.f;
+    const float scale = __fmul_rn(lrow, rcp_approx(__fsub_rn(s.hi, s.lo)));
+    const float ov = __fsub_rn(fminf(s.hi, jj + 1.f), fmaxf(s.lo, jj));
+    return ov > 0.f ? __fmul_rn(ov, scale) : 0.f;
 }
 
 __device__ __forceinline__ float chord2(const Ray2 &r, int ix, int iy) {
@@ -181,5 +217,18 @@ int launch_bp2d(const Geo2 &g, const float *r, float *out, const int *views, int
 int launch_cost2d(const Geo2 &g, const float *x, const int *views, int nv, const float *y,
                   WeightRef w, double *partials, int *nparts, cudaStream_t st);
 int bp2d_blocks(const Geo2 &g);
+
+int launch_fp3d(const Geo3 &g, const float *x, float *out, const int *views, int nv,
+                int mode, const float *y, WeightRef w, float gain, cudaStream_t st);
+int launch_bp3d(const Geo3 &g, const float *r, float *out, const int *views, int nv,
+                int mode, const UpdateArgs *ua, cudaStream_t st);
+int launch_cost3d(const Geo3 &g, const float *x, const int *views, int nv, const float *y,
+                  WeightRef w, double *partials, int *nparts, cudaStream_t st);
+int bp3d_blocks(const Geo3 &g);
+int launch_update3d(int nx, int ny, int nz, const float *x, float *xo, const float *zeta, const float *g,
+                    const void *D, int d_dtype, const float *dscale, const DevState *st, float beta,
+                    float inv_delta, int nbr, int curv_mode, cudaStream_t s);
+int launch_reg_value3d(int nx, int ny, int nz, const float *x, double beta, double delta, int nbr,
+                       double *partials, int *nparts, cudaStream_t s);
 
 }  // namespace oslalm

@@ -102,6 +102,59 @@ static void ray_table_view(const oslalm_geom_desc &d, int v, Ray2 *out) {
     }
 }
 
+// Cone-beam ray families of view v (FP64 set-up): transaxial line from the
+// source through detector column c, and the height fraction alpha(a).
+static void ray3_table_view(const oslalm_geom_desc &d, int v, Ray3 *out) {
+    double cu, su;
+    cos_sin_turns(view_turns(d, v), &cu, &su);
+    const double ex = -su, ey = cu;
+    const double sx = -d.dso * cu, sy = -d.dso * su;
+    const double xlo = d.offset_x - 0.5 * d.nx * d.dx;
+    const double ylo = d.offset_y - 0.5 * d.ny * d.dy;
+    for (int c = 0; c < d.ns; ++c) {
+        double s = ((double)c - (d.ns - 1) / 2.0 + d.offset_s) * d.ds;
+        double dxv = d.dsd * cu + s * ex, dyv = d.dsd * su + s * ey;
+        double ld = sqrt(dxv * dxv + dyv * dyv);
+        double ux = dxv / ld, uy = dyv / ld;
+        Ray3 r;
+        r.xy = make_ray2(d, sx, sy, ux, uy);
+        int axis = ray_axis(r.xy.packed);
+        double u_a = axis ? uy : ux;
+        double s_a = axis ? sy : sx;
+        double a_lo = axis ? ylo : xlo;
+        double da = axis ? d.dy : d.dx;
+        double alpha0 = (a_lo - s_a) / (u_a * ld);
+        double alpha1 = da / (u_a * ld);
+        double Z0 = alpha0 * d.dt / (2.0 * d.dz);
+        double W1 = alpha1 * d.dt / (4.0 * d.dz);  // Z1 / 2
+        // z0h: Z0 rounded to 15 significant bits
+        int e0;
+        frexp(Z0, &e0);
+        double z0h = Z0 == 0.0 ? 0.0 : ldexp(nearbyint(ldexp(Z0, 15 - e0)), e0 - 15);
+        r.z0h = (float)z0h;
+        r.z0l = (float)(Z0 - z0h);
+        // kw / 2^sw: W1 with |kw| < 512
+        int e1 = 0;
+        if (W1 != 0.0) frexp(W1, &e1);
+        int sw = 9 - e1;  // |W1| 2^sw in [256, 512)
+        if (sw > 30) sw = 30;
+        if (sw < 0) sw = 0;
+        int kw = (int)nearbyint(ldexp(W1, sw));
+        if (kw > 511) kw = 511;
+        if (kw < -511) kw = -511;
+        r.kw = kw;
+        r.sw = sw;
+        r.w1l = (float)(W1 - ldexp((double)kw, -sw));
+        // offset of the bottom face: zb = z/dz + nz/2 - offset_z/dz
+        double oz = 0.5 * d.nz - d.offset_z / d.dz;
+        double ozi = floor(oz);
+        r.oz_i = (int)ozi;
+        r.oz_f = (float)(oz - ozi);
+        r.q = (float)(d.dt / (2.0 * ld));
+        out[c] = r;
+    }
+}
+
 static int validate(const oslalm_geom_desc *d) {
     if (!d) return fail(OSLALM_ERR_ARG, "geometry descriptor is NULL");
     if (d->kind < 0 || d->kind > 2) return fail(OSLALM_ERR_ARG, "unknown geometry kind %d", d->kind);
@@ -122,6 +175,12 @@ static int validate(const oslalm_geom_desc *d) {
         double r = sqrt(hx * hx + hy * hy);
         if (!(r < d->dso && r < d->dsd - d->dso))
             return fail(OSLALM_ERR_ARG, "image box (radius %.3f mm) must lie inside the source circle and before the detector", r);
+        if (d->kind == OSLALM_CONE3D_FLAT) {
+            if (fabs(2.0 * d->offset_t - nearbyint(2.0 * d->offset_t)) > 1e-12)
+                return fail(OSLALM_ERR_ARG, "cone beam: offset_t must be a multiple of 1/2 row");
+            if (d->nt > 256) return fail(OSLALM_ERR_RANGE, "cone beam: at most 256 detector rows");
+            if (d->nz > 4096) return fail(OSLALM_ERR_RANGE, "cone beam: at most 4096 slices");
+        }
         double gmax = fabs((0.5 * d->ns + fabs(d->offset_s)) * d->ds / d->dsd);
         if (d->kind == OSLALM_FAN2D_ARC && gmax >= 1.2)
             return fail(OSLALM_ERR_RANGE, "fan angle too wide");
@@ -156,6 +215,26 @@ oslalm::Geo2 oslalm_geom::geo2() const {
     return o;
 }
 
+oslalm::Geo3 oslalm_geom::geo3() const {
+    Geo3 o;
+    o.nx = d.nx; o.ny = d.ny; o.nz = d.nz; o.ns = d.ns; o.nt = d.nt; o.nviews = d.nviews;
+    o.dx = (float)d.dx; o.dy = (float)d.dy; o.dz = (float)d.dz;
+    o.inv_dz = (float)(1.0 / d.dz);
+    o.zlo = (float)(d.offset_z - 0.5 * d.nz * d.dz);
+    o.xlo = (float)(d.offset_x - 0.5 * d.nx * d.dx);
+    o.ylo = (float)(d.offset_y - 0.5 * d.ny * d.dy);
+    o.dt = (float)d.dt;
+    o.t0 = (float)((d.nt - 1) / 2.0 - d.offset_t);
+    o.u0 = (int)nearbyint((d.nt - 1) - 2.0 * d.offset_t);
+    o.inv_ds = (float)(1.0 / d.ds);
+    o.c0 = (float)((d.ns - 1) / 2.0 - d.offset_s);
+    o.dso = (float)d.dso; o.dsd = (float)d.dsd;
+    o.half_diag = (float)(0.5 * sqrt(d.dx * d.dx + d.dy * d.dy));
+    o.rays = d_rays3;
+    o.views = d_views;
+    return o;
+}
+
 extern "C" {
 
 const char *oslalm_last_error(void) { return oslalm::g_err; }
@@ -176,8 +255,10 @@ int oslalm_geom_create(const oslalm_geom_desc *desc, oslalm_geom **out) {
     std::vector<View3> views3(d.nviews);
     std::vector<int> allv(d.nviews);
     std::vector<Ray2> rays;
+    std::vector<Ray3> rays3;
     bool two_d = d.kind != OSLALM_CONE3D_FLAT;
     if (two_d) rays.resize((size_t)d.nviews * d.ns);
+    else rays3.resize((size_t)d.nviews * d.ns);
     for (int v = 0; v < d.nviews; ++v) {
         double cu, su;
         cos_sin_turns(view_turns(d, v), &cu, &su);
@@ -185,9 +266,10 @@ int oslalm_geom_create(const oslalm_geom_desc *desc, oslalm_geom **out) {
         views3[v] = View3{(float)cu, (float)su, (float)(-d.dso * cu), (float)(-d.dso * su)};
         allv[v] = v;
         if (two_d) ray_table_view(d, v, &rays[(size_t)v * d.ns]);
+        else ray3_table_view(d, v, &rays3[(size_t)v * d.ns]);
     }
     auto cleanup = [&](int code, const char *what, cudaError_t e) {
-        cudaFree(g->d_rays); cudaFree(g->d_views); cudaFree(g->d_views3); cudaFree(g->d_allviews);
+        cudaFree(g->d_rays); cudaFree(g->d_rays3); cudaFree(g->d_views); cudaFree(g->d_views3); cudaFree(g->d_allviews);
         delete g;
         return fail(code, "%s: %s", what, cudaGetErrorString(e));
     };
@@ -196,10 +278,12 @@ int oslalm_geom_create(const oslalm_geom_desc *desc, oslalm_geom **out) {
     if ((e = cudaMalloc(&g->d_views3, sizeof(View3) * d.nviews)) != cudaSuccess) return cleanup(OSLALM_ERR_ALLOC, "cudaMalloc views3", e);
     if ((e = cudaMalloc(&g->d_allviews, sizeof(int) * d.nviews)) != cudaSuccess) return cleanup(OSLALM_ERR_ALLOC, "cudaMalloc views", e);
     if (two_d && (e = cudaMalloc(&g->d_rays, sizeof(Ray2) * rays.size())) != cudaSuccess) return cleanup(OSLALM_ERR_ALLOC, "cudaMalloc rays", e);
+    if (!two_d && (e = cudaMalloc(&g->d_rays3, sizeof(Ray3) * rays3.size())) != cudaSuccess) return cleanup(OSLALM_ERR_ALLOC, "cudaMalloc rays3", e);
     if ((e = cudaMemcpy(g->d_views, views.data(), sizeof(View2) * d.nviews, cudaMemcpyHostToDevice)) != cudaSuccess) return cleanup(OSLALM_ERR_CUDA, "upload", e);
     if ((e = cudaMemcpy(g->d_views3, views3.data(), sizeof(View3) * d.nviews, cudaMemcpyHostToDevice)) != cudaSuccess) return cleanup(OSLALM_ERR_CUDA, "upload", e);
     if ((e = cudaMemcpy(g->d_allviews, allv.data(), sizeof(int) * d.nviews, cudaMemcpyHostToDevice)) != cudaSuccess) return cleanup(OSLALM_ERR_CUDA, "upload", e);
     if (two_d && (e = cudaMemcpy(g->d_rays, rays.data(), sizeof(Ray2) * rays.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return cleanup(OSLALM_ERR_CUDA, "upload", e);
+    if (!two_d && (e = cudaMemcpy(g->d_rays3, rays3.data(), sizeof(Ray3) * rays3.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return cleanup(OSLALM_ERR_CUDA, "upload", e);
     *out = g;
     return OSLALM_OK;
 }
@@ -226,6 +310,7 @@ int oslalm_geom_destroy(oslalm_geom *g) {
     clear_error();
     if (!g) return OSLALM_OK;
     cudaFree(g->d_rays);
+    cudaFree(g->d_rays3);
     cudaFree(g->d_views);
     cudaFree(g->d_views3);
     cudaFree(g->d_allviews);

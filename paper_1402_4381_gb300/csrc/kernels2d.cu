@@ -61,6 +61,11 @@ __device__ __forceinline__ ACC march2(const Geo2 &g, const Ray2 &rp, const float
     for (int ia = ia0 + first; ia <= ia1; ia += stride) {
         const RowSpan s = row_span(rp, ia);
         const float jlo = floorf(s.lo), jhi = floorf(s.hi);
+        if (jlo == jhi) {  // the row stays inside one pixel: full row length
+            const int j = s.base + (int)jlo;
+            if ((unsigned)j < (unsigned)Nb) acc += (ACC)rp.lrow * (ACC)__ldg(x + (size_t)ia * sa + (size_t)j * sb);
+            continue;
+        }
         for (float jj = jlo; jj <= jhi; jj += 1.f) {
             const int j = s.base + (int)jj;
             if ((unsigned)j < (unsigned)Nb) {
@@ -155,59 +160,6 @@ __device__ __forceinline__ void channel_window(const Geo2 &g, const View2 &vw, f
     c1 = min(g.ns - 1, (int)floorf(cc + hw + kMargin));
 }
 
-__device__ __forceinline__ double rho_of_l(int l, double rho_min) {
-    if (l == 0) return 1.0;
-    const double pi = 3.14159265358979323846;
-    double a = pi / (double)(l + 1);
-    double b = pi / (double)(2 * l + 2);
-    double v = a * sqrt(1.0 - b * b);
-    return v > rho_min ? v : rho_min;
-}
-
-// Last block of a grid: reduce the per-block xi partials in a fixed order and
-// advance the continuation state (one thread).
-__device__ void finish_subset_iteration(const UpdateArgs &ua, int nblocks) {
-    __shared__ double red[32];
-    double v = 0.0;
-    for (int i = threadIdx.x + blockDim.x * threadIdx.y; i < nblocks; i += blockDim.x * blockDim.y)
-        v += __ldcg(ua.partials + i);
-    v = block_sum2d(v, red);
-    if (threadIdx.x == 0 && threadIdx.y == 0) {
-        DevState *st = ua.state;
-        const double xi = v;
-        const double rho_used = st->rho;
-        const int j = st->j;
-        int l = st->l;
-        int restart = 0;
-        double rho = rho_used;
-        if (ua.rho_mode == OSLALM_RHO_CONTINUATION) {
-            restart = xi > 0.0;
-        } else if (ua.rho_mode == OSLALM_RHO_REPLAY) {
-            restart = (ua.replay && j < ua.replay_n) ? (ua.replay[j] != 0) : 0;
-        }
-        if (ua.rho_mode != OSLALM_RHO_FIXED) {
-            l = restart ? 0 : l + 1;
-            rho = rho_of_l(l, ua.rho_min);
-        }
-        st->xi = xi;
-        st->l = l;
-        st->rho = rho;
-        if (ua.stats && ua.stats_cap > 0) {
-            oslalm_stats rec;
-            rec.xi = xi;
-            rec.rho_used = rho_used;
-            rec.l = l;
-            rec.restart = restart;
-            rec.subset = ua.subset;
-            rec.pad = 0;
-            ua.stats[j % ua.stats_cap] = rec;
-        }
-        st->j = j + 1;
-        st->counter = 0;
-        __threadfence();
-    }
-}
-
 template <int MODE>
 __global__ void __launch_bounds__(256) bp2d_kernel(Geo2 g, const float *__restrict__ r, float *__restrict__ out,
                                                    const int *__restrict__ views, int nv, UpdateArgs ua) {
@@ -255,21 +207,7 @@ __global__ void __launch_bounds__(256) bp2d_kernel(Geo2 g, const float *__restri
             ua.g[p] = a * acc + b * g_old;
             xi_local = (double)(g_old - acc) * (double)(acc - z_old);
         }
-        __shared__ double red[32];
-        __shared__ int is_last;
-        double bs = block_sum2d(xi_local, red);
-        const int nblocks = gridDim.x * gridDim.y;
-        if (threadIdx.x == 0 && threadIdx.y == 0) {
-            ua.partials[blockIdx.y * gridDim.x + blockIdx.x] = bs;
-            __threadfence();
-            unsigned t = atomicAdd(&ua.state->counter, 1u);
-            is_last = (t == (unsigned)(nblocks - 1));
-        }
-        __syncthreads();
-        if (is_last) {
-            __threadfence();
-            finish_subset_iteration(ua, nblocks);
-        }
+        subset_iteration_epilogue(ua, xi_local);
     }
 }
 

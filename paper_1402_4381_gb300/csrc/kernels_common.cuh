@@ -35,8 +35,8 @@ __device__ __forceinline__ double block_sum(double v) {
 // Sum over a 2D block (any shape up to 1024 threads) using caller scratch;
 // result valid in thread (0, 0).  Fixed order: deterministic.
 __device__ __forceinline__ double block_sum2d(double v, double *red) {
-    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
-    const int nt = blockDim.x * blockDim.y;
+    const int tid = (threadIdx.z * blockDim.y + threadIdx.y) * blockDim.x + threadIdx.x;
+    const int nt = blockDim.x * blockDim.y * blockDim.z;
     v = warp_sum(v);
     if ((tid & 31) == 0) red[tid >> 5] = v;
     __syncthreads();
@@ -61,6 +61,84 @@ __device__ __forceinline__ void nbr2d(int k, int &ox, int &oy) {
     const int idx = k < 4 ? k : k + 1;
     ox = idx % 3 - 1;
     oy = idx / 3 - 1;
+}
+
+// rho_l of the deterministic downward continuation (Eq. rho_l_formula_qp)
+__device__ __forceinline__ double rho_of_l(int l, double rho_min) {
+    if (l == 0) return 1.0;
+    const double pi = 3.14159265358979323846;
+    double a = pi / (double)(l + 1);
+    double b = pi / (double)(2 * l + 2);
+    double v = a * sqrt(1.0 - b * b);
+    return v > rho_min ? v : rho_min;
+}
+
+// Last block of a grid: reduce the per-block xi partials in a fixed order and
+// advance the continuation state (Sec. III-B): restart (l = 0) when xi > 0,
+// else l + 1; rho = rho_l.  One thread writes the state.
+__device__ __forceinline__ void finish_subset_iteration(const UpdateArgs &ua, int nblocks) {
+    __shared__ double red_last[32];
+    double v = 0.0;
+    const int nt = blockDim.x * blockDim.y * blockDim.z;
+    const int tid = (threadIdx.z * blockDim.y + threadIdx.y) * blockDim.x + threadIdx.x;
+    for (int i = tid; i < nblocks; i += nt) v += __ldcg(ua.partials + i);
+    v = block_sum2d(v, red_last);
+    if (tid == 0) {
+        DevState *st = ua.state;
+        const double xi = v;
+        const double rho_used = st->rho;
+        const int j = st->j;
+        int l = st->l;
+        int restart = 0;
+        double rho = rho_used;
+        if (ua.rho_mode == OSLALM_RHO_CONTINUATION) {
+            restart = xi > 0.0;
+        } else if (ua.rho_mode == OSLALM_RHO_REPLAY) {
+            restart = (ua.replay && j < ua.replay_n) ? (ua.replay[j] != 0) : 0;
+        }
+        if (ua.rho_mode != OSLALM_RHO_FIXED) {
+            l = restart ? 0 : l + 1;
+            rho = rho_of_l(l, ua.rho_min);
+        }
+        st->xi = xi;
+        st->l = l;
+        st->rho = rho;
+        if (ua.stats && ua.stats_cap > 0) {
+            oslalm_stats rec;
+            rec.xi = xi;
+            rec.rho_used = rho_used;
+            rec.l = l;
+            rec.restart = restart;
+            rec.subset = ua.subset;
+            rec.pad = 0;
+            ua.stats[j % ua.stats_cap] = rec;
+        }
+        st->j = j + 1;
+        st->counter = 0;
+        __threadfence();
+    }
+}
+
+// Block sum of the threads' xi contributions into the partials buffer; the
+// last block to arrive finishes the subset-iteration.  Called by every thread.
+__device__ __forceinline__ void subset_iteration_epilogue(const UpdateArgs &ua, double xi_local) {
+    __shared__ double red[32];
+    __shared__ int is_last;
+    const double bs = block_sum2d(xi_local, red);
+    const int nblocks = gridDim.x * gridDim.y * gridDim.z;
+    const int tid = (threadIdx.z * blockDim.y + threadIdx.y) * blockDim.x + threadIdx.x;
+    if (tid == 0) {
+        const int bid = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+        ua.partials[bid] = bs;
+        __threadfence();
+        unsigned t = atomicAdd(&ua.state->counter, 1u);
+        is_last = (t == (unsigned)(nblocks - 1));
+    }
+    __syncthreads();
+    if (is_last) {
+        __threadfence();
+        finish_subset_iteration(ua, nblocks);
+    }
 }
 
 }  // namespace oslalm

@@ -166,6 +166,21 @@ struct oslalm_problem {
 
 namespace {
 
+// geometry-generic projector / update launches
+int launch_fp_any(const oslalm_geom *g, const float *x, float *out, const int *views, int nv, int mode,
+                  const float *y, WeightRef w, float gain, cudaStream_t st) {
+    if (is_3d(g)) return launch_fp3d(g->geo3(), x, out, views, nv, mode, y, w, gain, st);
+    return launch_fp2d(g->geo2(), x, out, views, nv, mode, y, w, gain, st);
+}
+
+int launch_bp_any(const oslalm_geom *g, const float *r, float *out, const int *views, int nv, int mode,
+                  const UpdateArgs *ua, cudaStream_t st) {
+    if (is_3d(g)) return launch_bp3d(g->geo3(), r, out, views, nv, mode, ua, st);
+    return launch_bp2d(g->geo2(), r, out, views, nv, mode, ua, st);
+}
+
+int bp_blocks_any(const oslalm_geom *g) { return is_3d(g) ? bp3d_blocks(g->geo3()) : bp2d_blocks(g->geo2()); }
+
 int check_problem(const oslalm_problem *p) {
     if (!p) return fail(OSLALM_ERR_ARG, "problem handle is NULL");
     return OSLALM_OK;
@@ -181,7 +196,7 @@ WeightRef wref(const oslalm_problem *p, int m) {
 
 int fp_subset(oslalm_problem *p, const float *x, int m, int mode, float gain, cudaStream_t st) {
     const float *y = p->d_y + (size_t)p->off[m] * p->per_view;
-    return launch_fp2d(p->g->geo2(), x, p->d_r, p->d_views + p->off[m], p->cnt[m], mode, y, wref(p, m), gain, st);
+    return launch_fp_any(p->g, x, p->d_r, p->d_views + p->off[m], p->cnt[m], mode, y, wref(p, m), gain, st);
 }
 
 UpdateArgs update_args(oslalm_problem *p, int subset) {
@@ -229,7 +244,6 @@ int compute_denominator(oslalm_problem *p, cudaStream_t st) {
     const size_t npix = p->npix;
     fill_kernel<<<nblk(npix, 256), 256, 0, st>>>(p->d_xalt, npix, 1.f);
     OSL_CUDA_TRY(cudaMemsetAsync(p->d_g, 0, npix * sizeof(float), st));
-    Geo2 g2 = p->g->geo2();
     for (int m = 0; m < p->p.M; ++m) {
         if (p->cnt[m] == 0) continue;
         if (int rc = fp_subset(p, p->d_xalt, m, FP_PLAIN, 1.f, st)) return rc;
@@ -239,23 +253,34 @@ int compute_denominator(oslalm_problem *p, cudaStream_t st) {
         else if (w.dtype == OSLALM_F16) mul_weight_kernel<__half><<<nblk(nr, 256), 256, 0, st>>>(p->d_r, (const __half *)w.ptr, w.scale, nr);
         else mul_weight_kernel<__nv_bfloat16><<<nblk(nr, 256), 256, 0, st>>>(p->d_r, (const __nv_bfloat16 *)w.ptr, w.scale, nr);
         OSL_LAUNCH_CHECK("mul_weight");
-        if (int rc = launch_bp2d(g2, p->d_r, p->d_g, p->d_views + p->off[m], p->cnt[m], BP_ACCUM, nullptr, st)) return rc;
+        if (int rc = launch_bp_any(p->g, p->d_r, p->d_g, p->d_views + p->off[m], p->cnt[m], BP_ACCUM, nullptr, st))
+            return rc;
     }
     if (int rc = store_scaled(p, p->d_g, p->d_D, p->p.d_dtype, p->d_dscale, npix, st)) return rc;
     p->d_valid = true;
     return OSLALM_OK;
 }
 
+int update_step(oslalm_problem *p, const float *x_in, float *x_out, cudaStream_t st) {
+    const oslalm_geom_desc &d = p->g->d;
+    if (is_3d(p->g))
+        return launch_update3d(d.nx, d.ny, d.nz, x_in, x_out, p->d_zeta, p->d_g, p->d_D, p->p.d_dtype, p->d_dscale,
+                               p->d_state, (float)p->p.beta, (float)(1.0 / p->p.delta), p->p.nbr, p->p.curvature,
+                               st);
+    return launch_update2d(d.nx, d.ny, x_in, x_out, p->d_zeta, p->d_g, p->d_D, p->p.d_dtype, p->d_dscale,
+                           p->d_state, (float)p->p.beta, (float)(1.0 / p->p.delta), p->p.nbr, p->p.curvature, st);
+}
+
+int bp_update(oslalm_problem *p, int next, cudaStream_t st) {
+    UpdateArgs ua = update_args(p, next);
+    return launch_bp_any(p->g, p->d_r, nullptr, p->d_views + p->off[next], p->cnt[next], BP_UPDATE, &ua, st);
+}
+
 // one subset-iteration: x_in -> x_out, gradient of subset `next`
 int subset_iteration(oslalm_problem *p, const float *x_in, float *x_out, int next, cudaStream_t st) {
-    const oslalm_geom_desc &d = p->g->d;
-    if (int rc = launch_update2d(d.nx, d.ny, x_in, x_out, p->d_zeta, p->d_g, p->d_D, p->p.d_dtype, p->d_dscale,
-                                 p->d_state, (float)p->p.beta, (float)(1.0 / p->p.delta), p->p.nbr,
-                                 p->p.curvature, st))
-        return rc;
+    if (int rc = update_step(p, x_in, x_out, st)) return rc;
     if (int rc = fp_subset(p, x_out, next, FP_RESID, (float)p->p.M, st)) return rc;
-    UpdateArgs ua = update_args(p, next);
-    return launch_bp2d(p->g->geo2(), p->d_r, nullptr, p->d_views + p->off[next], p->cnt[next], BP_UPDATE, &ua, st);
+    return bp_update(p, next, st);
 }
 
 // `iters` whole iterations starting at subset-iteration j0 (a multiple of M)
@@ -336,22 +361,20 @@ extern "C" {
 int oslalm_project(const oslalm_geom *g, const float *x, float *sino, const int *views, int nv, void *stream) {
     clear_error();
     if (!g || nv < 0 || (nv > 0 && (!x || !sino || !views))) return fail(OSLALM_ERR_ARG, "bad project arguments");
-    if (is_3d(g)) return fail(OSLALM_ERR_ARG, "3D projector not available in this build");
     WeightRef w{nullptr, OSLALM_F32, nullptr};
-    return launch_fp2d(g->geo2(), x, sino, views, nv, FP_PLAIN, nullptr, w, 1.f, (cudaStream_t)stream);
+    return launch_fp_any(g, x, sino, views, nv, FP_PLAIN, nullptr, w, 1.f, (cudaStream_t)stream);
 }
 
 int oslalm_backproject(const oslalm_geom *g, const float *sino, float *x, const int *views, int nv, int accumulate,
                        void *stream) {
     clear_error();
     if (!g || nv < 0 || !x || (nv > 0 && (!sino || !views))) return fail(OSLALM_ERR_ARG, "bad backproject arguments");
-    if (is_3d(g)) return fail(OSLALM_ERR_ARG, "3D back-projector not available in this build");
     cudaStream_t st = (cudaStream_t)stream;
     if (nv == 0) {
-        if (!accumulate) OSL_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(float) * g->d.nx * g->d.ny, st));
+        if (!accumulate) OSL_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(float) * g->d.nx * g->d.ny * g->d.nz, st));
         return OSLALM_OK;
     }
-    return launch_bp2d(g->geo2(), sino, x, views, nv, accumulate ? BP_ACCUM : BP_STORE, nullptr, st);
+    return launch_bp_any(g, sino, x, views, nv, accumulate ? BP_ACCUM : BP_STORE, nullptr, st);
 }
 
 int oslalm_problem_create(const oslalm_geom *g, const float *y, const float *w, const oslalm_params *prm,
@@ -361,16 +384,17 @@ int oslalm_problem_create(const oslalm_geom *g, const float *y, const float *w, 
     *out = nullptr;
     if (!g || !y || !w || !prm) return fail(OSLALM_ERR_ARG, "NULL argument");
     const oslalm_params &pp = *prm;
-    if (is_3d(g)) return fail(OSLALM_ERR_ARG, "3D problems not available in this build");
     if (pp.M <= 0 || pp.M > g->d.nviews) return fail(OSLALM_ERR_ARG, "need 0 < M <= nviews (M=%d)", pp.M);
     if (!(pp.beta >= 0) || !(pp.delta > 0)) return fail(OSLALM_ERR_ARG, "need beta >= 0 and delta > 0");
-    if (pp.nbr != 4 && pp.nbr != 8) return fail(OSLALM_ERR_ARG, "2D neighbourhood must be 4 or 8");
+    if (!is_3d(g) && pp.nbr != 4 && pp.nbr != 8) return fail(OSLALM_ERR_ARG, "2D neighbourhood must be 4 or 8");
+    if (is_3d(g) && pp.nbr != 6 && pp.nbr != 26) return fail(OSLALM_ERR_ARG, "3D neighbourhood must be 6 or 26");
     if (pp.n_inner != 1) return fail(OSLALM_ERR_RANGE, "only n_inner = 1 is implemented");
     if (pp.rho_mode < 0 || pp.rho_mode > 2) return fail(OSLALM_ERR_ARG, "bad rho_mode");
     if (pp.rho_mode == OSLALM_RHO_FIXED && !(pp.rho_fixed > 0)) return fail(OSLALM_ERR_ARG, "rho_fixed must be > 0");
     if (pp.rho_mode != OSLALM_RHO_FIXED && !(pp.rho_min > 0 && pp.rho_min <= 1)) return fail(OSLALM_ERR_ARG, "need 0 < rho_min <= 1");
     if (pp.w_dtype < 0 || pp.w_dtype > 2 || pp.d_dtype < 0 || pp.d_dtype > 2) return fail(OSLALM_ERR_ARG, "bad dtype");
     if (pp.curvature != OSLALM_CURV_HUBER && pp.curvature != OSLALM_CURV_MAX) return fail(OSLALM_ERR_ARG, "bad curvature");
+    int p_n_partials_tmp = 0;
     oslalm_problem *p = new (std::nothrow) oslalm_problem();
     if (!p) return fail(OSLALM_ERR_ALLOC, "host allocation failed");
     p->g = g;
@@ -391,7 +415,17 @@ int oslalm_problem_create(const oslalm_geom *g, const float *y, const float *w, 
     size_t nsino = (size_t)d.nviews * p->per_view;
     size_t nr = (size_t)std::max(p->max_cnt, 1) * p->per_view;
     // cost: one partial per 128 rays of every subset plus the regularizer blocks
-    p->n_partials = (int)nblk(nsino, 128) + pp.M + bp2d_blocks(g->geo2()) + 64;
+    {
+        const oslalm_geom_desc &dd = g->d;
+        long reg_blocks = (long)((dd.nx + 31) / 32) * ((dd.ny + 7) / 8) * dd.nz;
+        long np = (long)nblk(nsino, 128) + pp.M + std::max<long>(reg_blocks, bp_blocks_any(g)) + 64;
+        if (np > (1L << 30)) {
+            delete p;
+            return fail(OSLALM_ERR_RANGE, "problem too large");
+        }
+        p_n_partials_tmp = (int)np;
+    }
+    p->n_partials = p_n_partials_tmp;
     cudaError_t e = cudaSuccess;
 #define OSL_ALLOC(ptr, bytes) \
     if (e == cudaSuccess) e = cudaMalloc((void **)&(ptr), (bytes))
@@ -452,7 +486,7 @@ int oslalm_init(oslalm_problem *p, const float *x, void *stream) {
     const int m0 = p->order[0];
     if (int rc = fp_subset(p, x, m0, FP_RESID, (float)p->p.M, st)) return rc;
     UpdateArgs ua = update_args(p, m0);
-    if (int rc = launch_bp2d(p->g->geo2(), p->d_r, nullptr, p->d_views + p->off[m0], p->cnt[m0], BP_INIT, &ua, st))
+    if (int rc = launch_bp_any(p->g, p->d_r, nullptr, p->d_views + p->off[m0], p->cnt[m0], BP_INIT, &ua, st))
         return rc;
     const double rho0 = p->p.rho_mode == OSLALM_RHO_FIXED ? p->p.rho_fixed : 1.0;
     set_state_kernel<<<1, 1, 0, st>>>(p->d_state, rho0, 0, 0);
@@ -505,7 +539,6 @@ int oslalm_profile_iterate(oslalm_problem *p, float *x, int n_iter, double *ms_o
     const long nsub = (long)n_iter * M;
     std::vector<cudaEvent_t> ev(6 * nsub);
     for (auto &e : ev) OSL_CUDA_TRY(cudaEventCreate(&e));
-    const oslalm_geom_desc &d = p->g->d;
     float *cur = x, *nxt = p->d_xalt;
     int rc = OSLALM_OK;
     long k = 0;
@@ -513,18 +546,13 @@ int oslalm_profile_iterate(oslalm_problem *p, float *x, int n_iter, double *ms_o
         for (int q = 0; q < M && !rc; ++q, ++k) {
             int next = p->order[(q + 1) % M];
             cudaEventRecord(ev[6 * k + 0], st);
-            rc = launch_update2d(d.nx, d.ny, cur, nxt, p->d_zeta, p->d_g, p->d_D, p->p.d_dtype, p->d_dscale,
-                                 p->d_state, (float)p->p.beta, (float)(1.0 / p->p.delta), p->p.nbr, p->p.curvature,
-                                 st);
+            rc = update_step(p, cur, nxt, st);
             cudaEventRecord(ev[6 * k + 1], st);
             cudaEventRecord(ev[6 * k + 2], st);
             if (!rc) rc = fp_subset(p, nxt, next, FP_RESID, (float)M, st);
             cudaEventRecord(ev[6 * k + 3], st);
             cudaEventRecord(ev[6 * k + 4], st);
-            UpdateArgs ua = update_args(p, next);
-            if (!rc)
-                rc = launch_bp2d(p->g->geo2(), p->d_r, nullptr, p->d_views + p->off[next], p->cnt[next], BP_UPDATE,
-                                 &ua, st);
+            if (!rc) rc = bp_update(p, next, st);
             cudaEventRecord(ev[6 * k + 5], st);
             std::swap(cur, nxt);
         }
@@ -578,22 +606,28 @@ int oslalm_cost(oslalm_problem *p, const float *x, double *out, void *stream) {
     if (int rc = check_problem(p)) return rc;
     if (!x || !out) return fail(OSLALM_ERR_ARG, "NULL argument");
     cudaStream_t st = (cudaStream_t)stream;
-    Geo2 g2 = p->g->geo2();
     int used = 0;
     for (int m = 0; m < p->p.M; ++m) {
         int np = 0;
         const float *y = p->d_y + (size_t)p->off[m] * p->per_view;
         if (used + (int)nblk((size_t)p->cnt[m] * p->per_view, 128) > p->n_partials)
             return fail(OSLALM_ERR_RANGE, "cost partial buffer too small");
-        if (int rc = launch_cost2d(g2, x, p->d_views + p->off[m], p->cnt[m], y, wref(p, m), p->d_partials + used, &np, st))
-            return rc;
+        int rc = is_3d(p->g) ? launch_cost3d(p->g->geo3(), x, p->d_views + p->off[m], p->cnt[m], y, wref(p, m),
+                                             p->d_partials + used, &np, st)
+                             : launch_cost2d(p->g->geo2(), x, p->d_views + p->off[m], p->cnt[m], y, wref(p, m),
+                                             p->d_partials + used, &np, st);
+        if (rc) return rc;
         used += np;
     }
-    if (used + bp2d_blocks(p->g->geo2()) > p->n_partials) return fail(OSLALM_ERR_RANGE, "cost partial buffer too small");
-    int np = 0;
     const oslalm_geom_desc &d = p->g->d;
-    if (int rc = launch_reg_value2d(d.nx, d.ny, x, p->p.beta, p->p.delta, p->p.nbr, p->d_partials + used, &np, st))
-        return rc;
+    if (used + (long)((d.nx + 31) / 32) * ((d.ny + 7) / 8) * d.nz > p->n_partials)
+        return fail(OSLALM_ERR_RANGE, "cost partial buffer too small");
+    int np = 0;
+    int rcr = is_3d(p->g) ? launch_reg_value3d(d.nx, d.ny, d.nz, x, p->p.beta, p->p.delta, p->p.nbr,
+                                               p->d_partials + used, &np, st)
+                          : launch_reg_value2d(d.nx, d.ny, x, p->p.beta, p->p.delta, p->p.nbr, p->d_partials + used,
+                                               &np, st);
+    if (rcr) return rcr;
     used += np;
     std::vector<double> h(used);
     OSL_CUDA_TRY(cudaMemcpyAsync(h.data(), p->d_partials, sizeof(double) * used, cudaMemcpyDeviceToHost, st));

@@ -28,30 +28,34 @@ def decode(packed):
     return axis, n0, k
 
 
+def _fma32(a, b, c):
+    """float32 fused multiply-add (the product of two float32 values is exact
+    in float64; one rounding of the sum to float32)."""
+    return (np.asarray(a, np.float64) * np.asarray(b, np.float64) + np.asarray(c, np.float64)).astype(F)
+
+
 def chords_float32(tab, c, ia, jb):
     """Length of ray c inside pixels (ia, jb) (major, minor indices), with the
-    float32 operations of the device code in the same order."""
+    float32 operations of the device code in the same order (the device's
+    approximate reciprocal is replaced by an exact one here)."""
     f0, kl, lrow = F(tab["f0"][c]), F(tab["kappa_lo"][c]), F(tab["lrow"][c])
     axis, n0, k = decode(tab["packed"][c:c + 1])
     n0, k = int(n0[0]), int(k[0])
     ia = ia.astype(np.int32)
-    p0 = ia * np.int32(k)
-    p1 = p0 + np.int32(k)
-    q0, q1 = p0 >> 11, p1 >> 11
-    r0 = (p0 & 2047).astype(F) * F(4.8828125e-4)
-    r1 = (p1 & 2047).astype(F) * F(4.8828125e-4)
-    w0 = (f0 + r0).astype(F) + (ia.astype(F) * kl).astype(F)
-    w1 = (f0 + r1).astype(F) + ((ia + 1).astype(F) * kl).astype(F)
-    w1 = (w1 + (q1 - q0).astype(F)).astype(F)
-    base = n0 + q0
-    lo, hi = np.minimum(w0, w1), np.maximum(w0, w1)
-    width = (hi - lo).astype(F)
-    with np.errstate(divide="ignore"):
-        scale = np.where(width > F(1e-30), ((F(1) / width).astype(F) * lrow).astype(F), F(0))
+    p = (2 * ia + 1) * np.int32(k)
+    q = p >> 12
+    fr = ((p & 4095).astype(F) * F(2.0 ** -12)).astype(F)
+    cc = _fma32(ia.astype(F) + F(0.5), kl, (f0 + fr).astype(F))
+    hw = np.abs(_fma32(F(k), F(2.0 ** -12), (F(0.5) * kl).astype(F)))
+    lo, hi = (cc - hw).astype(F), (cc + hw).astype(F)
+    base = n0 + q
     jj = (jb - base).astype(F)
+    jl, jh = np.floor(lo), np.floor(hi)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        scale = (lrow * (F(1) / (hi - lo).astype(F))).astype(F)
     ov = (np.minimum(hi, jj + F(1)) - np.maximum(lo, jj)).astype(F)
-    ch = np.where(scale > 0, np.where(ov > 0, (ov * scale).astype(F), F(0)),
-                  np.where(np.floor(lo) == jj, lrow, F(0)))
+    split = np.where(ov > 0, (ov * scale).astype(F), F(0))
+    ch = np.where(jl == jh, np.where(jj == jl, lrow, F(0)), split)
     return ch.astype(np.float64), int(axis[0])
 
 
