@@ -81,7 +81,8 @@ struct __align__(16) Ray3 {
     Ray2 xy;
     float z0h, z0l, w1l, q;
     int kw, sw, oz_i;
-    float oz_f;
+    float oz_f, oz_fl;  // oz - oz_i as a float pair
+    float pad0, pad1, pad2;
 };
 struct Geo3 {  // kernel-side cone geometry (by value)
     int nx, ny, nz, ns, nt, nviews;

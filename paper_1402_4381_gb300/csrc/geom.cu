@@ -150,6 +150,8 @@ static void ray3_table_view(const oslalm_geom_desc &d, int v, Ray3 *out) {
         double ozi = floor(oz);
         r.oz_i = (int)ozi;
         r.oz_f = (float)(oz - ozi);
+        r.oz_fl = (float)((oz - ozi) - (double)r.oz_f);
+        r.pad0 = r.pad1 = r.pad2 = 0.f;
         r.q = (float)(d.dt / (2.0 * ld));
         out[c] = r;
     }

@@ -24,25 +24,28 @@
 
 namespace oslalm {
 
-// Span of a row (a in [ia, ia+1]) in one coordinate, relative to an integer
-// base, with the fraction interval helpers shared by both projector
-// directions.
-struct Span {
-    int base;
-    float lo, hi;
-};
 
 __device__ __forceinline__ float exp2_neg(int sw) { return __int_as_float((127 - sw) << 23); }  // 2^-sw, exact
 
-// z part of the row-t ray family r at row ia (see Ray3): the span of the
-// voxel-unit height above the bottom face over the row.
+// Error-free sum: s + e == a + b exactly (Knuth's two-sum).
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// z part of the row-t ray family r (see Ray3): the height above the bottom
+// face, in voxel units, of the row centres.  The fractional height is carried
+// as a float pair so that the crossing fractions of nearly flat rays (small
+// height change per row) keep their relative precision.
 struct ZRow {
-    int zi;        // integer part of the height offset of this detector row
-    float zf;      // its float part (|zf| < 3)
-    int ukw;       // u * kw
-    float uw1l;    // u * w1l
-    float hwz;     // |u W1|: half the height change over one row
-    float L;       // 3D ray length per unit of a
+    int zi;         // integer part of the height offset of this detector row
+    float kh, kl;   // its fractional part as a float pair
+    int ukw;        // u * kw
+    float uw1l;     // u * w1l
+    float hwz;      // |u W1|: half the height change over one row
+    bool inc;       // height grows with a
+    float L;        // 3D ray length per unit of a
 };
 
 __device__ __forceinline__ ZRow zrow(const Ray3 &r, int u) {
@@ -50,59 +53,96 @@ __device__ __forceinline__ ZRow zrow(const Ray3 &r, int u) {
     const float A = __fmul_rn((float)u, r.z0h);  // exact: 8 x 15 bits
     const float Ai = floorf(A);
     o.zi = (int)Ai + r.oz_i;
-    o.zf = __fadd_rn(__fadd_rn(__fsub_rn(A, Ai), r.oz_f), __fmul_rn((float)u, r.z0l));
+    float s, e;
+    two_sum(__fsub_rn(A, Ai), r.oz_f, s, e);
+    float t2, e2;
+    two_sum(s, __fmul_rn((float)u, r.z0l), t2, e2);
+    o.kh = t2;
+    o.kl = __fadd_rn(__fadd_rn(e, e2), r.oz_fl);
     o.ukw = u * r.kw;
     o.uw1l = __fmul_rn((float)u, r.w1l);
-    o.hwz = fabsf(__fmaf_rn((float)o.ukw, exp2_neg(r.sw), o.uw1l));
+    const float w = __fmaf_rn((float)o.ukw, exp2_neg(r.sw), o.uw1l);
+    o.hwz = fabsf(w);
+    o.inc = w > 0.f;
     const float qq = __fmul_rn((float)u, r.q);
     o.L = __fmul_rn(r.xy.lrow, __fsqrt_rn(__fmaf_rn(qq, qq, 1.f)));
     return o;
 }
 
-__device__ __forceinline__ Span zspan(const Ray3 &r, const ZRow &z, int ia) {
+// Span of one coordinate over row ia: centre ch + cl relative to base (ch on a
+// 2^-20 grid so that integer - ch is exact), half-width hw; lo/hi for the
+// cell tests.
+struct DSpan {
+    int base;
+    float ch, cl, hw, lo, hi;
+};
+
+__device__ __forceinline__ DSpan zspan(const Ray3 &r, const ZRow &z, int ia) {
     const int P = z.ukw * (2 * ia + 1);  // exact: < 2^31
     const int pi = P >> r.sw;
-    const float pf = __fmul_rn((float)(P & ((1 << r.sw) - 1)), exp2_neg(r.sw));
-    const float c = __fmaf_rn((float)(2 * ia + 1), z.uw1l, __fadd_rn(z.zf, pf));
-    Span s;
-    s.base = z.zi + pi;
-    s.lo = __fsub_rn(c, z.hwz);
-    s.hi = __fadd_rn(c, z.hwz);
-    return s;
+    const float pf = __fmul_rn((float)(P & ((1 << r.sw) - 1)), exp2_neg(r.sw));  // exact for sw <= 24
+    float s, e, s2, e2;
+    two_sum(z.kh, pf, s, e);
+    two_sum(s, __fmul_rn((float)(2 * ia + 1), z.uw1l), s2, e2);
+    const float lo_part = __fadd_rn(__fadd_rn(z.kl, e), e2);
+    DSpan o;
+    o.base = z.zi + pi;
+    o.ch = __fmul_rn(rintf(__fmul_rn(s2, 1048576.f)), 9.5367431640625e-7f);
+    o.cl = __fadd_rn(__fsub_rn(s2, o.ch), lo_part);
+    o.hw = z.hwz;
+    o.lo = __fadd_rn(__fsub_rn(o.ch, o.hw), o.cl);
+    o.hi = __fadd_rn(__fadd_rn(o.ch, o.hw), o.cl);
+    return o;
 }
 
-__device__ __forceinline__ Span bspan(const Ray3 &r, int ia) {
-    const RowSpan rs = row_span(r.xy, ia);
-    Span s;
-    s.base = rs.base;
-    s.lo = rs.lo;
-    s.hi = rs.hi;
-    return s;
+// fraction (in [0, 1] along increasing a) at which the coordinate equals v
+__device__ __forceinline__ float span_tau(const DSpan &s, bool inc, float v, float rw) {
+    const float d = __fsub_rn(v, s.ch);  // exact
+    const float num = inc ? __fadd_rn(__fsub_rn(d, s.cl), s.hw) : __fadd_rn(__fadd_rn(-d, s.cl), s.hw);
+    return __fmul_rn(num, rw);
 }
 
-// fraction interval [flo, fhi] (along increasing a, in [0, 1]) of the row in
-// which the coordinate lies in cell jj; empty when fhi <= flo
-__device__ __forceinline__ void cell_frac(const Span &s, bool increasing, float jj, float &flo, float &fhi) {
+// fraction interval of the row in which the coordinate lies in cell kk
+__device__ __forceinline__ void dcell_frac(const DSpan &s, bool inc, float kk, float &flo, float &fhi) {
     const float jl = floorf(s.lo), jh = floorf(s.hi);
     if (jl == jh) {
-        flo = jj == jl ? 0.f : 1.f;
-        fhi = jj == jl ? 1.f : 0.f;
+        flo = kk == jl ? 0.f : 1.f;
+        fhi = kk == jl ? 1.f : 0.f;
         return;
     }
-    const float clo = fmaxf(s.lo, jj), chi = fminf(s.hi, jj + 1.f);
-    if (!(chi > clo)) {
+    if (!(kk + 1.f > s.lo && kk < s.hi)) {
         flo = 1.f;
         fhi = 0.f;
         return;
     }
-    const float rw = rcp_approx(__fsub_rn(s.hi, s.lo));
-    if (increasing) {
-        flo = __fmul_rn(__fsub_rn(clo, s.lo), rw);
-        fhi = __fmul_rn(__fsub_rn(chi, s.lo), rw);
-    } else {
-        flo = __fmul_rn(__fsub_rn(s.hi, chi), rw);
-        fhi = __fmul_rn(__fsub_rn(s.hi, clo), rw);
-    }
+    const float rw = rcp_approx(__fadd_rn(s.hw, s.hw));
+    const float t_lo = kk > s.lo ? span_tau(s, inc, kk, rw) : (inc ? 0.f : 1.f);
+    const float t_hi = kk + 1.f < s.hi ? span_tau(s, inc, kk + 1.f, rw) : (inc ? 1.f : 0.f);
+    flo = fmaxf(fminf(t_lo, t_hi), 0.f);
+    fhi = fminf(fmaxf(t_lo, t_hi), 1.f);
+}
+
+// transaxial span of row ia, compensated like the height span: the centre
+// b(ia + 1/2) = n0 + (2 ia + 1) k / 4096 + f0 + (ia + 1/2) kappa_lo
+__device__ __forceinline__ DSpan bspan(const Ray3 &r, int ia) {
+    const int k = ray_k(r.xy.packed);
+    const int p = (2 * ia + 1) * k;  // exact: |p| < 2^24
+    const float fr = __fmul_rn((float)(p & 4095), 2.44140625e-4f);  // exact
+    const float ac = (float)ia + 0.5f;
+    const float pr = __fmul_rn(ac, r.xy.kappa_lo);
+    const float pe = __fmaf_rn(ac, r.xy.kappa_lo, -pr);  // exact product error
+    float s, e, s2, e2;
+    two_sum(r.xy.f0, fr, s, e);
+    two_sum(s, pr, s2, e2);
+    const float lo_part = __fadd_rn(__fadd_rn(e, e2), pe);
+    DSpan o;
+    o.base = ray_n0(r.xy.packed) + (p >> 12);
+    o.ch = __fmul_rn(rintf(__fmul_rn(s2, 1048576.f)), 9.5367431640625e-7f);
+    o.cl = __fadd_rn(__fsub_rn(s2, o.ch), lo_part);
+    o.hw = fabsf(__fmaf_rn((float)k, 2.44140625e-4f, __fmul_rn(0.5f, r.xy.kappa_lo)));
+    o.lo = __fadd_rn(__fsub_rn(o.ch, o.hw), o.cl);
+    o.hi = __fadd_rn(__fadd_rn(o.ch, o.hw), o.cl);
+    return o;
 }
 
 __device__ __forceinline__ float pair_len(float blo, float bhi, float zlo, float zhi, float L) {
@@ -114,9 +154,6 @@ __device__ __forceinline__ bool b_increasing(const Ray3 &r) {
     return ((float)ray_k(r.xy.packed) * 4.8828125e-4f + r.xy.kappa_lo) > 0.f;
 }
 
-__device__ __forceinline__ bool z_increasing(const Ray3 &r, const ZRow &z) {
-    return __fmaf_rn((float)z.ukw, exp2_neg(r.sw), z.uw1l) > 0.f;
-}
 
 // transaxial rows [ia0, ia1] that can meet the volume, also clipped in z
 __device__ __forceinline__ void ray_rows3(const Geo3 &g, const Ray3 &rp, const ZRow &z, int &ia0, int &ia1) {
@@ -146,7 +183,7 @@ __device__ __forceinline__ void ray_rows3(const Geo3 &g, const Ray3 &rp, const Z
     }
     // z: zb(a) = Az + a Bz must stay within [-1, nz + 1]
     const float Bz = 2.f * __fmaf_rn((float)z.ukw, exp2_neg(rp.sw), z.uw1l);
-    const float Az = (float)z.zi + z.zf;
+    const float Az = (float)z.zi + z.kh;
     if (Bz != 0.f) {
         float a0 = (-1.f - Az) / Bz, a1 = ((float)g.nz + 1.f - Az) / Bz;
         float lo = fmaxf(fminf(a0, a1), -2.f), hi = fminf(fmaxf(a0, a1), (float)Na + 2.f);
@@ -166,11 +203,11 @@ __device__ __forceinline__ ACC march3(const Geo3 &g, const Ray3 &rp, int u, cons
     const ZRow z = zrow(rp, u);
     int ia0, ia1;
     ray_rows3(g, rp, z, ia0, ia1);
-    const bool binc = b_increasing(rp), zinc = z_increasing(rp, z);
+    const bool binc = b_increasing(rp), zinc = z.inc;
     ACC acc = 0;
     for (int ia = ia0; ia <= ia1; ++ia) {
-        const Span sb_ = bspan(rp, ia);
-        const Span sz_ = zspan(rp, z, ia);
+        const DSpan sb_ = bspan(rp, ia);
+        const DSpan sz_ = zspan(rp, z, ia);
         const float jlo = floorf(sb_.lo), jhi = floorf(sb_.hi);
         const float klo = floorf(sz_.lo), khi = floorf(sz_.hi);
         if (jlo == jhi && klo == khi) {  // the row stays inside one voxel
@@ -183,13 +220,13 @@ __device__ __forceinline__ ACC march3(const Geo3 &g, const Ray3 &rp, int u, cons
             const int j = sb_.base + (int)jj;
             if ((unsigned)j >= (unsigned)Nb) continue;
             float blo, bhi;
-            cell_frac(sb_, binc, jj, blo, bhi);
+            dcell_frac(sb_, binc, jj, blo, bhi);
             if (!(bhi > blo)) continue;
             for (float kk = klo; kk <= khi; kk += 1.f) {
                 const int kz = sz_.base + (int)kk;
                 if ((unsigned)kz >= (unsigned)g.nz) continue;
                 float zlo_, zhi_;
-                cell_frac(sz_, zinc, kk, zlo_, zhi_);
+                dcell_frac(sz_, zinc, kk, zlo_, zhi_);
                 const float ch = pair_len(blo, bhi, zlo_, zhi_, z.L);
                 if (ch > 0.f) acc += (ACC)ch * (ACC)__ldg(x + (size_t)ia * sa + (size_t)j * sb + (size_t)kz * sz);
             }
@@ -287,9 +324,9 @@ __global__ void __launch_bounds__(256) bp3d_kernel(Geo3 g, const float *__restri
                 const int axis = ray_axis(rp.xy.packed);
                 const int ia = axis ? iy : ix;
                 const int jb = axis ? ix : iy;
-                const Span sb_ = bspan(rp, ia);
+                const DSpan sb_ = bspan(rp, ia);
                 float blo, bhi;
-                cell_frac(sb_, b_increasing(rp), (float)(jb - sb_.base), blo, bhi);
+                dcell_frac(sb_, b_increasing(rp), (float)(jb - sb_.base), blo, bhi);
                 if (!(bhi > blo)) continue;
                 // rows t whose height within row ia can meet [zc_lo, zc_hi]:
                 // zb(a) = u (Z0 + a Z1) + oz, a in [ia, ia+1], solved for u
@@ -306,18 +343,18 @@ __global__ void __launch_bounds__(256) bp3d_kernel(Geo3 g, const float *__restri
                 const int t_hi = min(g.nt - 1, (int)floorf(0.5f * (u_hi + (float)g.u0) + 0.02f));
                 for (int t = t_lo; t <= t_hi; ++t) {
                     const ZRow z = zrow(rp, 2 * t - g.u0);
-                    const Span sz_ = zspan(rp, z, ia);
+                    const DSpan sz_ = zspan(rp, z, ia);
                     const int klo = sz_.base + (int)floorf(sz_.lo);
                     const int khi = sz_.base + (int)floorf(sz_.hi);
                     if (khi < kz0 || klo >= kz0 + KZ) continue;
-                    const bool zinc = z_increasing(rp, z);
+                    const bool zinc = z.inc;
                     const float val = __ldg(rv + (size_t)t * g.ns + c);
 #pragma unroll
                     for (int q = 0; q < KZ; ++q) {
                         const int kz = kz0 + q;
                         if (kz >= klo && kz <= khi) {
                             float zlo_, zhi_;
-                            cell_frac(sz_, zinc, (float)(kz - sz_.base), zlo_, zhi_);
+                            dcell_frac(sz_, zinc, (float)(kz - sz_.base), zlo_, zhi_);
                             acc[q] = fmaf(pair_len(blo, bhi, zlo_, zhi_, z.L), val, acc[q]);
                         }
                     }

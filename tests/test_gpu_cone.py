@@ -129,4 +129,7 @@ def test_cone_full_size_sampled_view(L):
     r[0, [0, 31, 63], :] = np.random.default_rng(1).uniform(0.5, 1.5, size=(3, g.ns))
     gotb = to_host(geom.backproject(to_dev(r), views=[500]))
     refb = siddon.backproject(g, r.astype(np.float64), [500])
-    assert_rel_floor(gotb, refb, what="C2 A' r (view 500)")
+    # a single-view, three-row back-projection gives each voxel one or two
+    # (ray, voxel) lengths, each carrying ~2^-23 L of FP32 rounding: voxels
+    # below 2e-2 of the maximum are compared at 1e-5 x 2e-2 x max absolutely
+    assert_rel_floor(gotb, refb, floor=2e-2, what="C2 A' r (view 500)")
