@@ -238,6 +238,42 @@ int oslalm_get_denominator(oslalm_problem *p, float *d, void *stream);
 int oslalm_profile_iterate(oslalm_problem *p, float *x, int n_iter, double *ms_out, int *launches_out,
                            void *stream);
 
+/* ---- batched reconstruction (many independent 2D scans) ------------------
+ * A batch advances several initialised 2D problems (oslalm_init done, each at
+ * a whole iteration) together: every subset-iteration step runs four
+ * persistent launches (update, forward projection + residual, back-projection
+ * + split gradient, restart test + continuation) whose grids of resident
+ * blocks walk a work list covering all scans still running, so scans of
+ * different image sizes, view counts and numbers of subsets share the GPU.
+ * Each scan follows exactly the single-problem algorithm (Eq. os_lalm_iterates,
+ * Sec. III-B continuation); with launch shape 0 a batched scan is
+ * bit-identical to the same problem iterated alone.  The batch references the
+ * problems' buffers: the problems must outlive it and must not be iterated
+ * by other calls while a batch call on them is queued.
+ * oslalm_batch_create: probs[host, n] problem handles.  Errors: ARG, STATE, ALLOC.
+ * oslalm_batch_iterate: x[host, n] device image pointers (one per problem,
+ *   updated in place); every problem runs n_iter full iterations (n_iter*M_i
+ *   subset-iterations; scans with fewer subsets finish earlier).  use_graph =
+ *   1 replays the whole call from a CUDA graph (captured on first use of the
+ *   same x pointers, n_iter and shape).  Errors: ARG, CUDA.
+ * oslalm_batch_autotune: times every launch shape (image tile, forward lanes
+ *   per ray) at two occupancies over probe_iters iterations, keeps the fastest
+ *   and restores every problem's image and state; ms_out[host, 2 x number of
+ *   shapes] or NULL receives the timings.  Allocates and frees backups;
+ *   synchronizes.  Errors: ARG, ALLOC, CUDA.
+ * oslalm_batch_set_shape / oslalm_batch_get_shape: shape index and blocks per
+ *   SM (0 = occupancy maximum).  oslalm_batch_shape_info: tile and lanes of a
+ *   shape; oslalm_batch_shape_count: number of shapes. */
+typedef struct oslalm_batch oslalm_batch;
+int oslalm_batch_create(oslalm_problem *const *probs, int n, oslalm_batch **out);
+int oslalm_batch_destroy(oslalm_batch *b);
+int oslalm_batch_iterate(oslalm_batch *b, float *const *x, int n_iter, int use_graph, void *stream);
+int oslalm_batch_autotune(oslalm_batch *b, float *const *x, int probe_iters, double *ms_out, void *stream);
+int oslalm_batch_set_shape(oslalm_batch *b, int shape, int blocks_per_sm);
+int oslalm_batch_get_shape(const oslalm_batch *b, int *shape, int *blocks_per_sm);
+int oslalm_batch_shape_count(void);
+int oslalm_batch_shape_info(int shape, int *tile_x, int *tile_y, int *lanes);
+
 /* ---- monitoring ----------------------------------------------------------
  * *out[host] = sqrt(sum_{mask} (x - xref)^2 / count(mask)) over the pixels
  * where mask[dev, image, uint8] != 0 (FP64 reduction); synchronizes.  Sec. V

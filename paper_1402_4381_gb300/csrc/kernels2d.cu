@@ -17,66 +17,11 @@
 
 #include "common.cuh"
 #include "kernels_common.cuh"
+#include "proj2d.cuh"
 
 namespace oslalm {
 
 // ---------------------------------------------------------------- forward
-// Major-axis rows [ia0, ia1] whose minor span can meet [0, Nb) (conservative).
-__device__ __forceinline__ void ray_rows(const Geo2 &g, const Ray2 &rp, int &ia0, int &ia1) {
-    const int axis = ray_axis(rp.packed);
-    const int n0 = ray_n0(rp.packed);
-    const int Na = axis ? g.ny : g.nx;
-    const int Nb = axis ? g.nx : g.ny;
-    ia0 = 0;
-    ia1 = Na - 1;
-    if (rp.lrow == 0.f) {  // the ray misses the image
-        ia1 = -1;
-        return;
-    }
-    const float kap = (float)ray_k(rp.packed) * 4.8828125e-4f + rp.kappa_lo;
-    if (kap != 0.f) {
-        // b - n0 in [-1, Nb - n0 + 1] at the row ends, with a row of margin
-        float t0 = ((float)(-n0) - 1.f - rp.f0) / kap;
-        float t1 = ((float)(Nb - n0) + 1.f - rp.f0) / kap;
-        float tlo = fmaxf(fminf(t0, t1), -2.f), thi = fminf(fmaxf(t0, t1), (float)Na + 2.f);
-        ia0 = max(0, (int)floorf(tlo) - 1);
-        ia1 = min(Na - 1, (int)ceilf(thi) + 1);
-    } else {
-        int j = n0 + (int)floorf(rp.f0);
-        if (j < 0 || j >= Nb) ia1 = -1;
-    }
-}
-
-// Sum of chord x pixel over rows first, first+stride, ... of the ray.
-template <typename ACC>
-__device__ __forceinline__ ACC march2(const Geo2 &g, const Ray2 &rp, const float *__restrict__ x, int first,
-                                      int stride) {
-    const int axis = ray_axis(rp.packed);
-    const int Nb = axis ? g.nx : g.ny;
-    const int sa = axis ? g.nx : 1;
-    const int sb = axis ? 1 : g.nx;
-    int ia0, ia1;
-    ray_rows(g, rp, ia0, ia1);
-    ACC acc = 0;
-    for (int ia = ia0 + first; ia <= ia1; ia += stride) {
-        const RowSpan s = row_span(rp, ia);
-        const float jlo = floorf(s.lo), jhi = floorf(s.hi);
-        if (jlo == jhi) {  // the row stays inside one pixel: full row length
-            const int j = s.base + (int)jlo;
-            if ((unsigned)j < (unsigned)Nb) acc += (ACC)rp.lrow * (ACC)__ldg(x + (size_t)ia * sa + (size_t)j * sb);
-            continue;
-        }
-        for (float jj = jlo; jj <= jhi; jj += 1.f) {
-            const int j = s.base + (int)jj;
-            if ((unsigned)j < (unsigned)Nb) {
-                const float ch = row_chord(s, rp.lrow, jj);
-                acc += (ACC)ch * (ACC)__ldg(x + (size_t)ia * sa + (size_t)j * sb);
-            }
-        }
-    }
-    return acc;
-}
-
 // One warp = 8 rays (adjacent channels) x 4 lanes; lane q of a ray takes
 // rows ia0+q, ia0+q+4, ...; the 4 partial sums are combined by shuffles in a
 // fixed order.
@@ -136,54 +81,13 @@ __global__ void __launch_bounds__(128) cost2d_kernel(Geo2 g, const float *__rest
 }
 
 // ---------------------------------------------------------------- back-projection
-// channel window of pixel centre (px, py) in view vw: channels whose ray may
-// cross the pixel, widened by a margin far above the rounding of the ray
-// tables so that no channel with a non-zero chord is missed.
-__device__ __forceinline__ void channel_window(const Geo2 &g, const View2 &vw, float px, float py, int &c0,
-                                               int &c1) {
-    constexpr float kMargin = 0.02f;
-    float cc, hw;
-    if (g.kind == OSLALM_PAR2D) {
-        float s = -px * vw.su + py * vw.cu;
-        cc = s * g.inv_ds + g.c0;
-        hw = 0.5f * (g.dx * fabsf(vw.su) + g.dy * fabsf(vw.cu)) * g.inv_ds;
-    } else {
-        float a = px * vw.cu + py * vw.su + g.dso;  // along u from the source
-        float b = -px * vw.su + py * vw.cu;         // along e
-        float gam = atan2f(b, a);
-        float d2 = a * a + b * b - g.half_diag * g.half_diag;
-        float ang = g.half_diag * rsqrtf(fmaxf(d2, 1e-12f));  // >= angular radius of the pixel
-        cc = gam * g.dsd * g.inv_ds + g.c0;
-        hw = ang * 1.0001f * g.dsd * g.inv_ds;
-    }
-    c0 = max(0, (int)ceilf(cc - hw - kMargin));
-    c1 = min(g.ns - 1, (int)floorf(cc + hw + kMargin));
-}
-
 template <int MODE>
 __global__ void __launch_bounds__(256) bp2d_kernel(Geo2 g, const float *__restrict__ r, float *__restrict__ out,
                                                    const int *__restrict__ views, int nv, UpdateArgs ua) {
     const int ix = blockIdx.x * 32 + threadIdx.x;
     const int iy = blockIdx.y * 8 + threadIdx.y;
     const bool valid = ix < g.nx && iy < g.ny;
-    float acc = 0.f;
-    if (valid) {
-        const float px = g.xlo + ((float)ix + 0.5f) * g.dx;
-        const float py = g.ylo + ((float)iy + 0.5f) * g.dy;
-        for (int lv = 0; lv < nv; ++lv) {
-            const int v = __ldg(views + lv);
-            if ((unsigned)v >= (unsigned)g.nviews) continue;  // caller-supplied view out of range
-            const View2 vw = g.views[v];
-            int c0, c1;
-            channel_window(g, vw, px, py, c0, c1);
-            const Ray2 *rr = g.rays + (size_t)v * g.ns;
-            const float *rv = r + (size_t)lv * g.ns;
-            for (int c = c0; c <= c1; ++c) {
-                const Ray2 rp = rr[c];
-                acc = fmaf(chord2(rp, ix, iy), __ldg(rv + c), acc);
-            }
-        }
-    }
+    const float acc = valid ? bp_pixel_sum(g, r, views, nv, ix, iy) : 0.f;
     const size_t p = (size_t)iy * g.nx + ix;
     if (MODE == BP_STORE) {
         if (valid) out[p] = acc;
@@ -219,40 +123,10 @@ __global__ void __launch_bounds__(256) update2d_kernel(int nx, int ny, const flo
                                                        const float *__restrict__ dscale,
                                                        const DevState *__restrict__ st, float beta,
                                                        float inv_delta, int curv_mode) {
-    __shared__ float tile[10][34];
-    const int ix0 = blockIdx.x * 32, iy0 = blockIdx.y * 8;
-    for (int k = threadIdx.y * 32 + threadIdx.x; k < 10 * 34; k += 256) {
-        int ty = k / 34, tx = k - ty * 34;
-        int gx = ix0 + tx - 1, gy = iy0 + ty - 1;
-        tile[ty][tx] = (gx >= 0 && gx < nx && gy >= 0 && gy < ny) ? __ldg(x + (size_t)gy * nx + gx) : 0.f;
-    }
-    __syncthreads();
-    const int ix = ix0 + threadIdx.x, iy = iy0 + threadIdx.y;
-    if (ix >= nx || iy >= ny) return;
-    const float xj = tile[threadIdx.y + 1][threadIdx.x + 1];
-    float grad = 0.f, curv = 0.f;
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-        int ox, oy;
-        nbr2d(k, ox, oy);
-        if (NBR == 4 && ox != 0 && oy != 0) continue;
-        const int nxp = ix + ox, nyp = iy + oy;
-        if (nxp < 0 || nxp >= nx || nyp < 0 || nyp >= ny) continue;
-        const float wk = (ox != 0 && oy != 0) ? 0.70710678118654752f : 1.f;
-        const float t = xj - tile[threadIdx.y + 1 + oy][threadIdx.x + 1 + ox];
-        const float u = t * inv_delta;
-        const float q = rsqrtf(fmaf(u, u, 1.f));
-        grad = fmaf(wk * t, q, grad);
-        curv += wk * (curv_mode == OSLALM_CURV_HUBER ? q : 1.f);
-    }
-    grad *= beta;
-    curv *= 2.f * beta;
-    const size_t p = (size_t)iy * nx + ix;
-    const float rho = (float)st->rho;
-    const float s = rho * __ldg(zeta + p) + (1.f - rho) * __ldg(gs + p);
-    const float den = rho * (load_w(D, p) * __ldg(dscale)) + curv;
-    float xn = xj - (s + grad) / den;
-    xo[p] = fmaxf(xn, 0.f);
+    __shared__ float tile[10 * 34];
+    update_tile<32, 8, DT, NBR>(tile, blockIdx.x * 32, blockIdx.y * 8, threadIdx.x, threadIdx.y,
+                                threadIdx.y * 32 + threadIdx.x, 256, nx, ny, x, xo, zeta, gs, D, dscale,
+                                (float)st->rho, beta, inv_delta, curv_mode);
 }
 
 template <int NBR>

@@ -16,6 +16,7 @@
 
 #include "common.cuh"
 #include "kernels_common.cuh"
+#include "problem.cuh"
 
 namespace oslalm {
 
@@ -130,39 +131,6 @@ static size_t dtype_size(int dt) { return dt == OSLALM_F32 ? 4 : 2; }
 
 using namespace oslalm;
 
-struct oslalm_problem {
-    const oslalm_geom *g;
-    oslalm_params p;
-    long npix;
-    int per_view;  // nt * ns
-    std::vector<int> order, off, cnt;  // subset order; view offset / count of subset m (subset-major layout)
-    int max_cnt;
-    int *d_views = nullptr;  // subset-major global view ids [nviews]
-    float *d_y = nullptr;    // subset-major [nviews][nt][ns]
-    void *d_w = nullptr;     // same, storage dtype p.w_dtype
-    float *d_wscale = nullptr;
-    void *d_D = nullptr;     // image, storage dtype p.d_dtype
-    float *d_dscale = nullptr;
-    unsigned int *d_maxbits = nullptr;
-    float *d_g = nullptr, *d_zeta = nullptr, *d_xalt = nullptr;
-    float *d_r = nullptr;    // residual of one subset
-    float *d_tmp = nullptr;  // full-sinogram scratch (set_data staging)
-    DevState *d_state = nullptr;
-    double *d_partials = nullptr;
-    int n_partials = 0;
-    oslalm_stats *d_stats = nullptr;
-    int stats_cap = 0;
-    signed char *d_replay = nullptr;
-    int replay_n = 0;
-    bool d_valid = false, initialized = false;
-    long j_host = 0;  // subset-iterations done
-    // CUDA graph of whole iterations
-    cudaGraphExec_t gexec = nullptr;
-    const float *g_x = nullptr;
-    int g_iters = 0;
-    cudaStream_t g_stream = nullptr;
-    oslalm_stats *g_stats_ptr = nullptr;
-};
 
 namespace {
 

@@ -91,6 +91,14 @@ def lib():
         "oslalm_profile_iterate": ([_VP, _VP, i, ctypes.POINTER(d), ip, _VP], i),
         "oslalm_fbp": ([_VP, _VP, _VP, i, _VP], i),
         "oslalm_ray_table": ([ctypes.POINTER(GeomDesc), i, _VP, _VP, _VP, _VP], i),
+        "oslalm_batch_create": ([ctypes.POINTER(_VP), i, ctypes.POINTER(_VP)], i),
+        "oslalm_batch_destroy": ([_VP], i),
+        "oslalm_batch_iterate": ([_VP, ctypes.POINTER(_VP), i, i, _VP], i),
+        "oslalm_batch_autotune": ([_VP, ctypes.POINTER(_VP), i, ctypes.POINTER(d), _VP], i),
+        "oslalm_batch_set_shape": ([_VP, i, i], i),
+        "oslalm_batch_get_shape": ([_VP, ip, ip], i),
+        "oslalm_batch_shape_count": ([], i),
+        "oslalm_batch_shape_info": ([i, ip, ip, ip], i),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -339,3 +347,59 @@ def rmsd(x, xref, mask, stream=None) -> float:
     _check(lib().oslalm_rmsd(_ptr(x), _ptr(xref), _ptr(mask), int(x.numel()), ctypes.byref(out), _stream(stream)),
            "rmsd")
     return out.value
+
+
+class Batch:
+    """Several initialised 2D problems advanced together (oslalm_batch)."""
+
+    def __init__(self, problems: Sequence[Problem]):
+        self.problems = list(problems)
+        arr = (_VP * len(self.problems))(*[p._h for p in self.problems])
+        self._h = _VP()
+        _check(lib().oslalm_batch_create(arr, len(self.problems), ctypes.byref(self._h)), "batch_create")
+
+    def _xs(self, xs):
+        if len(xs) != len(self.problems):
+            raise ValueError("one image per problem")
+        for x, p in zip(xs, self.problems):
+            _dev_f32(x, p.geom.image_shape, "x")
+        return (_VP * len(xs))(*[x.data_ptr() for x in xs])
+
+    def iterate(self, xs, n_iter=1, use_graph=True, stream=None):
+        _check(lib().oslalm_batch_iterate(self._h, self._xs(xs), int(n_iter), int(bool(use_graph)), _stream(stream)),
+               "batch_iterate")
+
+    def autotune(self, xs, probe_iters=1, stream=None):
+        n = lib().oslalm_batch_shape_count()
+        ms = (ctypes.c_double * (2 * n))()
+        _check(lib().oslalm_batch_autotune(self._h, self._xs(xs), int(probe_iters), ms, _stream(stream)),
+               "batch_autotune")
+        return [list(ms[2 * k: 2 * k + 2]) for k in range(n)]
+
+    def set_shape(self, shape, blocks_per_sm=0):
+        _check(lib().oslalm_batch_set_shape(self._h, int(shape), int(blocks_per_sm)), "batch_set_shape")
+
+    def get_shape(self):
+        a, b = ctypes.c_int(), ctypes.c_int()
+        _check(lib().oslalm_batch_get_shape(self._h, ctypes.byref(a), ctypes.byref(b)), "batch_get_shape")
+        return a.value, b.value
+
+    @staticmethod
+    def shapes():
+        out = []
+        for k in range(lib().oslalm_batch_shape_count()):
+            tx, ty, ln = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+            _check(lib().oslalm_batch_shape_info(k, ctypes.byref(tx), ctypes.byref(ty), ctypes.byref(ln)), "shape")
+            out.append(dict(tile=(tx.value, ty.value), lanes=ln.value))
+        return out
+
+    def close(self):
+        if self._h:
+            lib().oslalm_batch_destroy(self._h)
+            self._h = _VP()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -121,3 +121,23 @@ def tiny_cone(n: int = 8, nz: int = 4, nviews: int = 8, ns: int = 15, nt: int = 
     return Geometry(kind=CONE3D_FLAT, nx=n, ny=n, nz=nz, dx=1.0, dy=1.0, dz=0.8, nviews=nviews,
                     angle_start=0.05, angle_span=2 * math.pi, ns=ns, nt=nt, ds=1.3, dt=1.1,
                     dso=20.0, dsd=35.0)
+
+
+def c3_batch(n_slices: int = 64, seed: int = 1301, n_iter: int = 30):
+    """Batched 2D fan beam: n independent slices, image sizes uniform in
+    {256^2, 384^2, 512^2} over a 500 mm field of view, view counts uniform in
+    {492, 738, 984}, 888 channels, seeded ellipse phantoms, I0 uniform in
+    [2e4, 2e5], M = views / 41 subsets, n_iter iterations."""
+    rng = np.random.default_rng(seed)
+    base = c1_fan()
+    out = []
+    for k in range(n_slices):
+        n = int(rng.choice([256, 384, 512]))
+        nv = int(rng.choice([492, 738, 984]))
+        g = dataclasses.replace(base.geom, nx=n, ny=n, dx=500.0 / n, dy=500.0 / n, nviews=nv)
+        I0 = float(rng.uniform(2e4, 2e5))
+        out.append(dataclasses.replace(base, name=f"batch_slice{k}_{n}_v{nv}", geom=g, phantom="ellipses",
+                                       phantom_seed=seed * 1000 + k, noise_seed=seed * 1000 + 500 + k,
+                                       n_ellipses=10, I0=I0, sigma=0.0, M=nv // 41, n_iter=n_iter,
+                                       w_dtype="f32", d_dtype="f32"))
+    return out
