@@ -274,6 +274,40 @@ int oslalm_batch_get_shape(const oslalm_batch *b, int *shape, int *blocks_per_sm
 int oslalm_batch_shape_count(void);
 int oslalm_batch_shape_info(int shape, int *tile_x, int *tile_y, int *lanes);
 
+/* ---- learned warm start (no counterpart in the paper) ----------------------
+ * A 4-level U-Net (3x3 convs with 32/64/128/256 channels, ReLU, 2x2 average
+ * pooling, nearest 2x upsampling, skip concatenation, 1x1 output conv plus
+ * the input as a residual; 1,946,305 parameters) mapping an FBP image to an
+ * estimate of the converged PWLS image, used as the initial image x0 of
+ * OS-LALM (the minimiser is unchanged).  BF16 activations and weights, FP32
+ * accumulation on the tensor cores, FP32 master weights, Adam
+ * (beta 0.9 / 0.999, eps 1e-8), mean-squared-error loss.
+ * Images are FP32 [n][height][width] on the device; the network sees
+ * x * scale (scale ~ 1/mu_water puts water at 1) and returns y / scale.
+ * oslalm_cnn_create: buffers for exactly `batch` images of height x width
+ *   (multiples of 8); seeded He-normal initialisation.  Errors: ARG, ALLOC.
+ * oslalm_cnn_param_count: parameters in the exchange layout of get/set:
+ *   per layer (e0a, e0b, e1a, e1b, e2a, e2b, b3a, b3b, d2a, d2b, d1a, d1b, d0a,
+ *   d0b) weights [cout][3][3][cin] then biases [cout]; then out.w[32], out.b.
+ * oslalm_cnn_get_params / oslalm_cnn_set_params: host copies (set also resets
+ *   the Adam state).  oslalm_cnn_forward: y[dev] = net(x[dev]).
+ * oslalm_cnn_gradients: loss and parameter gradients (host, exchange layout)
+ *   without an update.  oslalm_cnn_train_step: one Adam step on (x, target);
+ *   *loss (host, may be NULL; when given the call synchronizes).
+ * oslalm_cnn_flops_per_image: multiply-add count x 2 of one forward pass. */
+typedef struct oslalm_cnn oslalm_cnn;
+long oslalm_cnn_param_count(void);
+int oslalm_cnn_create(int batch, int height, int width, unsigned long long seed, oslalm_cnn **out);
+int oslalm_cnn_destroy(oslalm_cnn *c);
+int oslalm_cnn_get_params(oslalm_cnn *c, float *host);
+int oslalm_cnn_set_params(oslalm_cnn *c, const float *host);
+int oslalm_cnn_forward(oslalm_cnn *c, const float *x, float *y, int n, float scale, void *stream);
+int oslalm_cnn_gradients(oslalm_cnn *c, const float *x, const float *target, int n, float scale, float *grad_host,
+                         double *loss, void *stream);
+int oslalm_cnn_train_step(oslalm_cnn *c, const float *x, const float *target, int n, float scale, float lr,
+                          double *loss, void *stream);
+double oslalm_cnn_flops_per_image(int height, int width);
+
 /* ---- monitoring ----------------------------------------------------------
  * *out[host] = sqrt(sum_{mask} (x - xref)^2 / count(mask)) over the pixels
  * where mask[dev, image, uint8] != 0 (FP64 reduction); synchronizes.  Sec. V

@@ -99,6 +99,15 @@ def lib():
         "oslalm_batch_get_shape": ([_VP, ip, ip], i),
         "oslalm_batch_shape_count": ([], i),
         "oslalm_batch_shape_info": ([i, ip, ip, ip], i),
+        "oslalm_cnn_param_count": ([], ctypes.c_long),
+        "oslalm_cnn_create": ([i, i, i, ctypes.c_ulonglong, ctypes.POINTER(_VP)], i),
+        "oslalm_cnn_destroy": ([_VP], i),
+        "oslalm_cnn_get_params": ([_VP, _VP], i),
+        "oslalm_cnn_set_params": ([_VP, _VP], i),
+        "oslalm_cnn_forward": ([_VP, _VP, _VP, i, ctypes.c_float, _VP], i),
+        "oslalm_cnn_gradients": ([_VP, _VP, _VP, i, ctypes.c_float, _VP, ctypes.POINTER(d), _VP], i),
+        "oslalm_cnn_train_step": ([_VP, _VP, _VP, i, ctypes.c_float, ctypes.c_float, ctypes.POINTER(d), _VP], i),
+        "oslalm_cnn_flops_per_image": ([i, i], d),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -396,6 +405,98 @@ class Batch:
     def close(self):
         if self._h:
             lib().oslalm_batch_destroy(self._h)
+            self._h = _VP()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# the exchange layout of the network parameters (matches include/oslalm.h)
+CNN_LAYERS = [("e0a", 1, 32), ("e0b", 32, 32), ("e1a", 32, 64), ("e1b", 64, 64), ("e2a", 64, 128),
+              ("e2b", 128, 128), ("b3a", 128, 256), ("b3b", 256, 256), ("d2a", 384, 128), ("d2b", 128, 128),
+              ("d1a", 192, 64), ("d1b", 64, 64), ("d0a", 96, 32), ("d0b", 32, 32)]
+
+
+def cnn_flatten(params: dict) -> np.ndarray:
+    """dict of arrays (names 'e0a.w' [co,3,3,ci], 'e0a.b', ..., 'out.w', 'out.b') -> flat float32."""
+    parts = []
+    for name, _, _ in CNN_LAYERS:
+        parts += [np.asarray(params[name + ".w"]).ravel(), np.asarray(params[name + ".b"]).ravel()]
+    parts += [np.asarray(params["out.w"]).ravel(), np.asarray(params["out.b"]).ravel()]
+    return np.concatenate(parts).astype(np.float32)
+
+
+def cnn_unflatten(flat: np.ndarray) -> dict:
+    out, k = {}, 0
+    for name, ci, co in CNN_LAYERS:
+        n = co * 9 * ci
+        out[name + ".w"] = flat[k:k + n].reshape(co, 3, 3, ci)
+        k += n
+        out[name + ".b"] = flat[k:k + co]
+        k += co
+    out["out.w"] = flat[k:k + 32]
+    out["out.b"] = flat[k + 32:k + 33]
+    return out
+
+
+class WarmStartNet:
+    """The warm-start U-Net (oslalm_cnn) for batches of `batch` images."""
+
+    def __init__(self, batch, height, width, seed=0):
+        self.batch, self.height, self.width = batch, height, width
+        self._h = _VP()
+        _check(lib().oslalm_cnn_create(int(batch), int(height), int(width), int(seed), ctypes.byref(self._h)),
+               "cnn_create")
+
+    @staticmethod
+    def param_count():
+        return int(lib().oslalm_cnn_param_count())
+
+    def get_params(self) -> np.ndarray:
+        out = np.zeros(self.param_count(), np.float32)
+        _check(lib().oslalm_cnn_get_params(self._h, out.ctypes.data), "cnn_get_params")
+        return out
+
+    def set_params(self, flat):
+        flat = np.ascontiguousarray(flat, dtype=np.float32)
+        assert flat.size == self.param_count()
+        _check(lib().oslalm_cnn_set_params(self._h, flat.ctypes.data), "cnn_set_params")
+
+    def forward(self, x, scale, out=None, stream=None):
+        import torch
+        _dev_f32(x, (self.batch, self.height, self.width), "x")
+        if out is None:
+            out = torch.empty_like(x)
+        _check(lib().oslalm_cnn_forward(self._h, _ptr(x), _ptr(out), self.batch, float(scale), _stream(stream)),
+               "cnn_forward")
+        return out
+
+    def gradients(self, x, target, scale, stream=None):
+        _dev_f32(x, (self.batch, self.height, self.width), "x")
+        _dev_f32(target, (self.batch, self.height, self.width), "target")
+        g = np.zeros(self.param_count(), np.float32)
+        loss = ctypes.c_double()
+        _check(lib().oslalm_cnn_gradients(self._h, _ptr(x), _ptr(target), self.batch, float(scale), g.ctypes.data,
+                                          ctypes.byref(loss), _stream(stream)), "cnn_gradients")
+        return loss.value, g
+
+    def train_step(self, x, target, scale, lr, want_loss=True, stream=None):
+        loss = ctypes.c_double()
+        _check(lib().oslalm_cnn_train_step(self._h, _ptr(x), _ptr(target), self.batch, float(scale), float(lr),
+                                           ctypes.byref(loss) if want_loss else None, _stream(stream)),
+               "cnn_train_step")
+        return loss.value if want_loss else None
+
+    @staticmethod
+    def flops_per_image(height, width):
+        return float(lib().oslalm_cnn_flops_per_image(int(height), int(width)))
+
+    def close(self):
+        if self._h:
+            lib().oslalm_cnn_destroy(self._h)
             self._h = _VP()
 
     def __del__(self):
