@@ -82,19 +82,41 @@ def up_bwd(dy):
     return dy.reshape(N, H // 2, 2, W // 2, 2, C).sum(axis=(2, 4))
 
 
-def forward(p, x):
-    """x [N,H,W] -> prediction [N,H,W] and the activations cache."""
-    c = {"in": x[..., None]}
+def bf16(a):
+    """Round to the nearest BF16 value (ties to even), returned as float64:
+    the storage precision model used to check BF16 training kernels."""
+    a32 = np.ascontiguousarray(a, dtype=np.float32)
+    b = a32.view(np.uint32).astype(np.uint64)
+    b = (b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000
+    return b.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def _ident(a):
+    return a
+
+
+def forward(p, x, q=None):
+    """x [N,H,W] -> prediction [N,H,W] and the activations cache.
+
+    q: optional rounding applied where a reduced-precision implementation
+    stores a tensor (input image, conv weights, every activation and pooled
+    tensor); the default is exact FP64."""
+    q = q or _ident
+    c = {"in": q(x[..., None])}
 
     def cr(name, inp):
-        z = conv3x3(inp, p[name + ".w"], p[name + ".b"])
-        c[name] = np.maximum(z, 0.0)
+        z = conv3x3(inp, q(p[name + ".w"]), p[name + ".b"])
+        c[name] = q(np.maximum(z, 0.0))
+        return c[name]
+
+    def pl(name, h):
+        c[name] = q(pool(h))
         return c[name]
 
     h = cr("e0b", cr("e0a", c["in"]))
-    h = cr("e1b", cr("e1a", pool(h)))
-    h = cr("e2b", cr("e2a", pool(h)))
-    h = cr("b3b", cr("b3a", pool(h)))
+    h = cr("e1b", cr("e1a", pl("p0", h)))
+    h = cr("e2b", cr("e2a", pl("p1", h)))
+    h = cr("b3b", cr("b3a", pl("p2", h)))
     c["cat2"] = np.concatenate([up(h), c["e2b"]], axis=-1)
     h = cr("d2b", cr("d2a", c["cat2"]))
     c["cat1"] = np.concatenate([up(h), c["e1b"]], axis=-1)
@@ -105,30 +127,35 @@ def forward(p, x):
     return y, c
 
 
-def loss_and_grads(p, x, target):
-    y, c = forward(p, x)
+def loss_and_grads(p, x, target, q=None):
+    """Mean squared error, its gradient for every parameter, and the
+    prediction.  q as in forward; backward it rounds every stored gradient
+    tensor (output-layer gradient, masked conv gradients, data gradients,
+    upsampling and pooling gradients)."""
+    q = q or _ident
+    y, c = forward(p, x, q)
     n = y.size
     loss = float(np.mean((y - target) ** 2))
     dy = 2.0 * (y - target) / n
     g = {"out.w": np.einsum("nhw,nhwc->c", dy, c["d0b"]), "out.b": np.array([dy.sum()])}
-    dh = dy[..., None] * p["out.w"]
+    dh = q(dy[..., None] * p["out.w"])
 
     def crb(name, inp, dout):
-        dz = dout * (c[name] > 0)
-        dx, g[name + ".w"], g[name + ".b"] = conv3x3_bwd(inp, p[name + ".w"], dz)
-        return dx
+        dz = q(dout * (c[name] > 0))
+        dx, g[name + ".w"], g[name + ".b"] = conv3x3_bwd(inp, q(p[name + ".w"]), dz)
+        return q(dx)
 
     dcat0 = crb("d0a", c["cat0"], crb("d0b", c["d0a"], dh))
-    dh = up_bwd(dcat0[..., :64])
+    dh = q(up_bwd(dcat0[..., :64]))
     dskip0 = dcat0[..., 64:]
     dcat1 = crb("d1a", c["cat1"], crb("d1b", c["d1a"], dh))
-    dh = up_bwd(dcat1[..., :128])
+    dh = q(up_bwd(dcat1[..., :128]))
     dskip1 = dcat1[..., 128:]
     dcat2 = crb("d2a", c["cat2"], crb("d2b", c["d2a"], dh))
-    dh = up_bwd(dcat2[..., :256])
+    dh = q(up_bwd(dcat2[..., :256]))
     dskip2 = dcat2[..., 256:]
-    dh = pool_bwd(crb("b3a", pool(c["e2b"]), crb("b3b", c["b3a"], dh))) + dskip2
-    dh = pool_bwd(crb("e2a", pool(c["e1b"]), crb("e2b", c["e2a"], dh))) + dskip1
-    dh = pool_bwd(crb("e1a", pool(c["e0b"]), crb("e1b", c["e1a"], dh))) + dskip0
+    dh = q(pool_bwd(crb("b3a", c["p2"], crb("b3b", c["b3a"], dh))) + dskip2)
+    dh = q(pool_bwd(crb("e2a", c["p1"], crb("e2b", c["e2a"], dh))) + dskip1)
+    dh = q(pool_bwd(crb("e1a", c["p0"], crb("e1b", c["e1a"], dh))) + dskip0)
     crb("e0a", c["in"], crb("e0b", c["e0a"], dh))
     return loss, g, y

@@ -1,11 +1,19 @@
 """GPU warm-start network (BF16 tensor-core kernels, FP32 accumulation)
-against the FP64 reference: forward output, loss and every parameter
+against the reference network: forward output, loss and every parameter
 gradient, parameter exchange, and that training lowers the loss.
 
-Tolerance (derived from the arithmetic): activations and weights are rounded
-to BF16 (8-bit significand, relative 2^-9) at every layer of a 14-layer
-network, so outputs and gradients agree to a few percent in relative L2
-norm: 5e-2 for the output correction and 1e-1 for each gradient tensor."""
+Two references.  (1) The reference with the kernels' BF16 storage model
+(every stored activation, weight and gradient tensor rounded to BF16): with
+parameters and images whose sums are exact in FP32 (small integers, sparse
++-1 weights, a power-of-two pixel count) the GPU must reproduce it exactly in
+the forward pass and to FP32 summation order in the weight gradients, at any
+size.  With general real parameters FP32 summation order moves some BF16
+roundings by one ulp and those flips cascade through 14 layers (a 1e-7
+relative perturbation before each rounding already moves the output by
+about 1.5% on 2x32x32); only the 8x8 case stays free of flips.  (2) The
+exact FP64 reference: BF16 storage keeps gradient tensors within about
+10-16% (relative L2) of exact, as the CPU test of the storage model
+measures; the bound here is 0.25 for gradients and 5e-2 for the output."""
 import numpy as np
 import pytest
 
@@ -47,26 +55,90 @@ def test_param_exchange_roundtrip(L):
     assert flat.size == C.n_params(p) == L.WarmStartNet.param_count()
 
 
+def _exact_params(seed):
+    """Sparse +-1 weights and integer biases: every conv sum of integer
+    images is an integer far below 2^24, hence exact in FP32."""
+    rng = np.random.default_rng(seed)
+    p = {}
+    for name, cin, cout in C.LAYERS:
+        mask = rng.random((cout, 3, 3, cin)) < 3.0 / (9 * cin)
+        sign = np.where(rng.random((cout, 3, 3, cin)) < 0.65, 1.0, -1.0)
+        p[name + ".w"] = mask * sign
+        p[name + ".b"] = rng.integers(0, 2, size=cout).astype(np.float64)
+    p["out.w"] = rng.integers(-1, 2, size=32).astype(np.float64)
+    p["out.b"] = np.array([1.0])
+    return p
+
+
+@pytest.mark.parametrize("shape", [(2, 32, 32), (1, 16, 64), (4, 8, 32)])
+def test_exact_case_reproduces_bf16_storage_model(L, shape):
+    import torch
+    n, h, w = shape
+    rng = np.random.default_rng(1)
+    x = rng.integers(0, 4, size=shape).astype(np.float32)
+    t = (x + rng.integers(-2, 3, size=shape)).astype(np.float32)
+    p = _exact_params(5)
+    net = L.WarmStartNet(n, h, w, seed=0)
+    net.set_params(L.cnn_flatten(p))
+    xd, td = torch.as_tensor(x, device="cuda"), torch.as_tensor(t, device="cuda")
+    y = net.forward(xd, 1.0).cpu().numpy().astype(np.float64)
+    loss_q, g_q, y_q = C.loss_and_grads(p, x.astype(np.float64), t.astype(np.float64), q=C.bf16)
+    assert np.array_equal(y, y_q)
+    loss, g = net.gradients(xd, td, 1.0)
+    assert abs(loss - loss_q) <= 1e-9 * loss_q
+    gd = L.cnn_unflatten(g)
+    bad = {k: v for k in g_q if not (v := _rel(gd[k].astype(np.float64), g_q[k])) < 1e-5}
+    assert not bad, bad
+
+
+def test_small_case_reproduces_bf16_storage_model(L):
+    """Real-valued parameters on 8x8: no rounding flips, so the GPU equals
+    the storage model to FP32 summation order."""
+    import torch
+    shape = (1, 8, 8)
+    rng = np.random.default_rng(7)
+    x = rng.uniform(0, 2, size=shape).astype(np.float32)
+    t = (x + rng.normal(0, 0.3, size=shape)).astype(np.float32)
+    p = _params()
+    net = L.WarmStartNet(1, 8, 8, seed=0)
+    net.set_params(L.cnn_flatten(p))
+    xd, td = torch.as_tensor(x, device="cuda"), torch.as_tensor(t, device="cuda")
+    y = net.forward(xd, 1.0).cpu().numpy().astype(np.float64)
+    x64 = x.astype(np.float64)
+    loss_q, g_q, y_q = C.loss_and_grads(p, x64, t.astype(np.float64), q=C.bf16)
+    assert _rel(y - x64, y_q - x64) < 1e-5
+    loss, g = net.gradients(xd, td, 1.0)
+    assert abs(loss - loss_q) <= 1e-5 * loss_q
+    gd = L.cnn_unflatten(g)
+    bad = {k: v for k in g_q if not (v := _rel(gd[k].astype(np.float64), g_q[k])) < 1e-5}
+    assert not bad, bad
+
+
 @pytest.mark.parametrize("shape", [(2, 32, 32), (1, 24, 40)])
-def test_forward_and_gradients_match_fp64(L, shape):
+def test_forward_and_gradients_within_bf16_bound_of_fp64(L, shape):
     import torch
     n, h, w = shape
     rng = np.random.default_rng(7)
-    x = rng.uniform(0, 2, size=shape)
-    t = x + rng.normal(0, 0.3, size=shape)
+    x = rng.uniform(0, 2, size=shape).astype(np.float32)
+    t = (x + rng.normal(0, 0.3, size=shape)).astype(np.float32)
     p = _params()
     net = L.WarmStartNet(n, h, w, seed=0)
     net.set_params(L.cnn_flatten(p))
-    xd = torch.as_tensor(x.astype(np.float32), device="cuda")
-    td = torch.as_tensor(t.astype(np.float32), device="cuda")
+    xd = torch.as_tensor(x, device="cuda")
+    td = torch.as_tensor(t, device="cuda")
     y = net.forward(xd, 1.0).cpu().numpy().astype(np.float64)
-    loss_ref, g_ref, y_ref = C.loss_and_grads(p, x.astype(np.float32).astype(np.float64), t.astype(np.float32))
-    assert _rel(y - x, y_ref - x) < 5e-2
+    x64, t64 = x.astype(np.float64), t.astype(np.float64)
+    loss_ref, g_ref, y_ref = C.loss_and_grads(p, x64, t64)
+    assert _rel(y - x64, y_ref - x64) < 5e-2
     loss, g = net.gradients(xd, td, 1.0)
     assert abs(loss - loss_ref) <= 2e-2 * loss_ref
     gd = L.cnn_unflatten(g)
-    for name in g_ref:
-        assert _rel(gd[name].astype(np.float64), g_ref[name]) < 1e-1, name
+    # d loss / d out.b = 2 mean(y - t): one sum whose terms cancel, so its
+    # error is exactly twice the mean forward error, not a relative one
+    db_err = abs(float(gd["out.b"][0]) - float(g_ref["out.b"][0]))
+    assert db_err <= 2.0 * abs(float(np.mean(y - y_ref))) * 1.01 + 1e-5
+    bad = {k: v for k in g_ref if k != "out.b" and not (v := _rel(gd[k].astype(np.float64), g_ref[k])) < 0.25}
+    assert not bad, bad
 
 
 def test_scale_is_applied(L):
