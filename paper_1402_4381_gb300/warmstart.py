@@ -1,25 +1,34 @@
 """Learned warm start for OS-LALM: dataset generation, training and
-evaluation on the fan-beam geometry.
+evaluation on a 2D fan-beam geometry.
 
-* scans: seeded random ellipse phantoms (water body plus 9 inner ellipses,
-  attenuation 0-0.04 /mm) on the 512^2 / 984-view / 888-channel fan beam,
-  I0 uniform in [2e4, 2e5], W = counts;
+* scans: seeded random ellipse phantoms (10 ellipses, attenuation
+  0-0.04 /mm) on the fan beam (512^2 image, 984 views, 888 channels at full
+  size), I0 uniform in [2e4, 2e5], W = counts;
 * input: the FBP image (clipped at 0); target: the OS-LALM image after
-  `target_iters` iterations from the FBP image (M = 24, continuation), both
-  computed with the library (the targets with the batched persistent path);
+  `target_iters` iterations from the FBP image (continuation, FP16 storage
+  of W and D), both computed by the library, the targets with the batched
+  persistent path;
 * network: the U-Net of oslalm_cnn (BF16 tensor-core training kernels),
-  Adam, mean-squared error in units of mu_water;
-* evaluation on held-out scans: x* from a decreasing-M schedule ending with
-  the convergent one-subset method; OS-LALM (M = 24, continuation, FP16
-  storage) from the FBP image and from the network's image; RMS difference
-  to x* in the field of view after every iteration; iterations and seconds
-  (CUDA events, network inference included) to reach each HU threshold.
-Host orchestration only: every arithmetic step runs in liboslalm.
+  Adam with a cosine learning-rate decay, mean-squared error in units of
+  the attenuation of water;
+* evaluation on held-out scans: x* from a decreasing-M schedule that ends
+  with the convergent one-subset method; OS-LALM from the FBP image and
+  from the network's image (clipped at 0); RMS difference to x* in the
+  field of view after every iteration; iterations and seconds (CUDA events,
+  network inference included) to reach each HU threshold.
+
+The minimiser is unchanged: the network only supplies x0, and FBP stays the
+fallback initial image.  Host orchestration only: every arithmetic step runs
+in liboslalm.
+
+Run: python -m paper_1402_4381_gb300.warmstart --train 2000 --test 100 --out result.json
 """
 from __future__ import annotations
 
+import argparse
 import concurrent.futures as cf
 import dataclasses
+import json
 import math
 import multiprocessing as mp
 import os
@@ -31,14 +40,24 @@ from . import synth, workloads as W
 
 SCALE = 1.0 / synth.MU_WATER  # network units: water = 1
 HU = synth.HU
+THRESHOLDS = (20.0, 10.0, 5.0, 2.0, 1.0)
+FULL_REF_SCHEDULE = ((24, 60), (8, 60), (2, 100), (1, 800))
 
 
-def scan_workload(seed: int, geom=None) -> W.Workload:
-    base = W.c1_fan()
-    g = geom if geom is not None else base.geom
+def base_workload(nx=512, nviews=984, ns=888, M=24) -> W.Workload:
+    """The fan-beam scan family (full size by default, or scaled with the
+    same field of view and fan angle)."""
+    wl = W.c1_fan()
+    if (nx, nviews, ns) != (wl.geom.nx, wl.geom.nviews, wl.geom.ns):
+        wl = W.scaled(wl, nx, nviews, ns, M, name_suffix=f"{nx}_v{nviews}")
+    return dataclasses.replace(wl, M=M)
+
+
+def scan_workload(seed: int, base: W.Workload) -> W.Workload:
+    g = base.geom
     rng = np.random.default_rng(10_000 + seed)
     I0 = float(rng.uniform(2e4, 2e5))
-    return dataclasses.replace(base, name=f"warm_{seed}", geom=g, phantom="ellipses", phantom_seed=20_000 + seed,
+    return dataclasses.replace(base, name=f"warm_{seed}", phantom="ellipses", phantom_seed=20_000 + seed,
                                noise_seed=30_000 + seed, n_ellipses=10, fov_radius=0.96 * g.nx * g.dx / 2,
                                I0=I0, sigma=0.0, w_dtype="f16", d_dtype="f16")
 
@@ -52,13 +71,14 @@ def make_scans(wls, workers=None):
     """Sinograms of the workloads (numpy, in a spawn-context process pool:
     call before the process touches the GPU)."""
     workers = workers or min(16, os.cpu_count() or 1)
-    if workers <= 1:
+    if workers <= 1 or len(wls) <= 2:
         return [_scan(w) for w in wls]
     with cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
         return list(ex.map(_scan, wls, chunksize=4))
 
 
 def fov_mask(g):
+    """Pixels inside the scanned field of view (radius dso sin(fan half-angle))."""
     ix = (np.arange(g.nx) - (g.nx - 1) / 2.0) * g.dx
     iy = (np.arange(g.ny) - (g.ny - 1) / 2.0) * g.dy
     Y, X = np.meshgrid(iy, ix, indexing="ij")
@@ -66,67 +86,62 @@ def fov_mask(g):
     return (np.sqrt(X * X + Y * Y) <= R)[None]
 
 
-def targets(oslalm, torch, geom, wls, scans, x0s, iters, chunk=64):
-    """OS-LALM images after `iters` iterations from x0, with the batched path."""
-    out = []
-    dev = x0s[0].device
+def _problem(oslalm, torch, geomh, wl, y, w, M=None, use_graph=True):
+    dev = torch.device("cuda", torch.cuda.current_device())
+    return oslalm.Problem(geomh, torch.as_tensor(y, device=dev), torch.as_tensor(w, device=dev), beta=wl.beta,
+                          delta=wl.delta, nbr=wl.nbr, M=M or wl.M, w_dtype=wl.w_dtype, d_dtype=wl.d_dtype,
+                          use_graph=use_graph)
+
+
+def run_batched(oslalm, torch, geomh, wls, scans, xs, schedule, chunk=64):
+    """Advance the images xs (in place) through `schedule` = ((M, iters), ...)
+    with the batched persistent path, `chunk` scans per batch; a new M
+    restarts the method (init) from the current image."""
     for k in range(0, len(wls), chunk):
-        probs, xs = [], []
-        for wl, (y, w), x0 in zip(wls[k:k + chunk], scans[k:k + chunk], x0s[k:k + chunk]):
-            p = oslalm.Problem(geom, torch.as_tensor(y, device=dev), torch.as_tensor(w, device=dev), beta=wl.beta,
-                               delta=wl.delta, nbr=wl.nbr, M=wl.M, w_dtype=wl.w_dtype, d_dtype=wl.d_dtype,
-                               use_graph=False)
-            x = x0.clone()
-            p.init(x)
-            probs.append(p)
-            xs.append(x)
-        b = oslalm.Batch(probs)
-        b.iterate(xs, iters, use_graph=False)
-        torch.cuda.synchronize()
-        out += xs
-        b.close()
-        for p in probs:
-            p.close()
-    return out
+        for M, iters in schedule:
+            probs = [_problem(oslalm, torch, geomh, wl, y, w, M=M, use_graph=False)
+                     for wl, (y, w) in zip(wls[k:k + chunk], scans[k:k + chunk])]
+            for p, x in zip(probs, xs[k:k + chunk]):
+                p.init(x)
+            b = oslalm.Batch(probs)
+            b.iterate(xs[k:k + chunk], iters, use_graph=True)
+            torch.cuda.synchronize()
+            b.close()
+            for p in probs:
+                p.close()
+    return xs
 
 
-def reference_image(oslalm, torch, geom, wl, y, w, x0, schedule=((24, 60), (8, 60), (2, 100), (1, 800))):
-    x = x0.clone()
-    for M, n in schedule:
-        p = oslalm.Problem(geom, y, w, beta=wl.beta, delta=wl.delta, nbr=wl.nbr, M=M, use_graph=True)
-        p.init(x)
-        p.iterate(x, n)
-        p.close()
-    return x
-
-
-def train(oslalm, torch, net, xs, ts, epochs, lr, batch, seed=0, log=None):
+def train(torch, net, xs, ts, epochs, lr, batch, seed=0, log=None):
+    """Adam on shuffled mini-batches, cosine decay of the learning rate.
+    Returns (first-batch loss per epoch, steps, seconds)."""
     n = len(xs)
     rng = np.random.default_rng(seed)
-    X = torch.stack(xs)
-    T = torch.stack(ts)
-    hist = []
-    steps = 0
+    X = torch.stack([x.reshape(x.shape[-2:]) for x in xs])
+    T = torch.stack([t.reshape(t.shape[-2:]) for t in ts])
+    hist, steps = [], 0
+    torch.cuda.synchronize()
     t0 = time.time()
     for ep in range(epochs):
-        perm = rng.permutation(n)
+        perm = torch.as_tensor(rng.permutation(n), device=X.device)
         lr_e = lr * 0.5 * (1 + math.cos(math.pi * ep / epochs))
-        losses = []
+        first = None
         for k in range(0, n - batch + 1, batch):
-            idx = torch.as_tensor(perm[k:k + batch], device=X.device)
+            idx = perm[k:k + batch]
             xb = X.index_select(0, idx).contiguous()
             tb = T.index_select(0, idx).contiguous()
-            losses.append(net.train_step(xb, tb, SCALE, lr_e, want_loss=(k == 0)))
+            l = net.train_step(xb, tb, SCALE, lr_e, want_loss=(k == 0))
+            first = l if k == 0 else first
             steps += 1
-        hist.append(float(losses[0]))
+        hist.append(float(first))
         if log:
-            log(f"epoch {ep}: loss {losses[0]:.4e} lr {lr_e:.2e}")
+            log(f"epoch {ep}: loss {first:.4e} lr {lr_e:.2e}")
     torch.cuda.synchronize()
     return hist, steps, time.time() - t0
 
 
-def evaluate(oslalm, torch, geom, wls, scans, x0s, xstars, mask_np, init_fn=None, n_iter=50,
-             thresholds=(20.0, 10.0, 5.0, 2.0, 1.0)):
+def evaluate(oslalm, torch, geomh, wls, scans, x0s, xstars, mask_np, init_fn=None, n_iter=50,
+             thresholds=THRESHOLDS):
     """Per scan: RMSD curve (HU) of OS-LALM from x0 (or init_fn(x0)), and the
     iterations / seconds to reach each threshold."""
     dev = x0s[0].device
@@ -134,10 +149,9 @@ def evaluate(oslalm, torch, geom, wls, scans, x0s, xstars, mask_np, init_fn=None
     stream = torch.cuda.current_stream()
     rows = []
     for wl, (y, w), x0, xs in zip(wls, scans, x0s, xstars):
-        p = oslalm.Problem(geom, torch.as_tensor(y, device=dev), torch.as_tensor(w, device=dev), beta=wl.beta,
-                           delta=wl.delta, nbr=wl.nbr, M=wl.M, w_dtype=wl.w_dtype, d_dtype=wl.d_dtype,
-                           use_graph=True)
+        p = _problem(oslalm, torch, geomh, wl, y, w)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
         e0.record(stream)
         x = init_fn(x0) if init_fn else x0.clone()
         p.init(x)
@@ -145,7 +159,7 @@ def evaluate(oslalm, torch, geom, wls, scans, x0s, xstars, mask_np, init_fn=None
         e1.synchronize()
         t = e0.elapsed_time(e1)
         curve = [oslalm.rmsd(x, xs, mask) / HU]
-        reached = {}
+        reached = {th: (0, t / 1000.0) for th in thresholds if curve[0] <= th}
         for k in range(1, n_iter + 1):
             e0.record(stream)
             p.iterate(x, 1)
@@ -157,71 +171,120 @@ def evaluate(oslalm, torch, geom, wls, scans, x0s, xstars, mask_np, init_fn=None
             for th in thresholds:
                 if th not in reached and r <= th:
                     reached[th] = (k, t / 1000.0)
-        for th in thresholds:
-            if th not in reached and curve[0] <= th:
-                reached[th] = (0, 0.0)
         rows.append(dict(curve=curve, reached=reached))
         p.close()
     return rows
 
 
-def summarize(rows, thresholds=(20.0, 10.0, 5.0, 2.0, 1.0)):
-    out = {"rmsd_hu_iter0": float(np.mean([r["curve"][0] for r in rows])),
-           "rmsd_hu_last": float(np.mean([r["curve"][-1] for r in rows])), "thresholds": {}}
+def summarize(rows, thresholds=THRESHOLDS):
+    curves = np.array([r["curve"] for r in rows])
+    out = {"rmsd_hu_mean_by_iteration": [round(float(v), 3) for v in curves.mean(axis=0)], "thresholds": {}}
     for th in thresholds:
         hit = [r["reached"][th] for r in rows if th in r["reached"]]
         out["thresholds"][f"{th:g}"] = {
-            "reached": f"{len(hit)}/{len(rows)}",
+            "reached": len(hit), "of": len(rows),
             "mean_iterations": float(np.mean([h[0] for h in hit])) if hit else None,
             "mean_seconds": float(np.mean([h[1] for h in hit])) if hit else None,
         }
     return out
 
 
-def experiment(n_train=256, n_test=16, target_iters=200, epochs=30, batch=8, lr=1e-3, geom=None, n_eval_iter=50,
-               log=print):
+def paired_gain(fbp_rows, cnn_rows, thresholds=THRESHOLDS):
+    """Per threshold, over the scans where both starts reach it: mean
+    iterations and seconds saved by the network's initial image."""
+    out = {}
+    for th in thresholds:
+        both = [(f["reached"][th], c["reached"][th]) for f, c in zip(fbp_rows, cnn_rows)
+                if th in f["reached"] and th in c["reached"]]
+        only_cnn = sum(1 for f, c in zip(fbp_rows, cnn_rows) if th in c["reached"] and th not in f["reached"])
+        out[f"{th:g}"] = {
+            "scans_both": len(both), "scans_only_cnn": only_cnn,
+            "iterations_fbp": float(np.mean([b[0][0] for b in both])) if both else None,
+            "iterations_cnn": float(np.mean([b[1][0] for b in both])) if both else None,
+            "seconds_fbp": float(np.mean([b[0][1] for b in both])) if both else None,
+            "seconds_cnn": float(np.mean([b[1][1] for b in both])) if both else None,
+        }
+    return out
+
+
+def experiment(n_train=2000, n_test=100, target_iters=200, epochs=30, batch=8, lr=1e-3, nx=512, nviews=984,
+               ns=888, M=24, ref_schedule=FULL_REF_SCHEDULE, n_eval_iter=50, chunk=64, log=print):
     """The whole warm-start experiment; returns a JSON-ready dict."""
-    wls_tr = [scan_workload(s, geom) for s in range(n_train)]
-    wls_te = [scan_workload(100_000 + s, geom) for s in range(n_test)]
+    base = base_workload(nx, nviews, ns, M)
+    wls_tr = [scan_workload(s, base) for s in range(n_train)]
+    wls_te = [scan_workload(1_000_000 + s, base) for s in range(n_test)]
     t0 = time.time()
     scans_tr = make_scans(wls_tr)
     scans_te = make_scans(wls_te)
     t_scan = time.time() - t0
+    log(f"scans: {t_scan:.1f} s")
     import torch
     from . import oslalm
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
-    g = wls_tr[0].geom
+    g = base.geom
     geomh = oslalm.Geometry(g)
     x0_tr = [geomh.fbp(torch.as_tensor(y, device=dev), clip=True) for y, _ in scans_tr]
     x0_te = [geomh.fbp(torch.as_tensor(y, device=dev), clip=True) for y, _ in scans_te]
-    t0 = time.time()
-    tg = targets(oslalm, torch, geomh, wls_tr, scans_tr, x0_tr, target_iters)
     torch.cuda.synchronize()
+    t0 = time.time()
+    targets = run_batched(oslalm, torch, geomh, wls_tr, scans_tr, [x.clone() for x in x0_tr],
+                          ((M, target_iters),), chunk)
     t_targets = time.time() - t0
+    log(f"targets: {t_targets:.1f} s")
     net = oslalm.WarmStartNet(batch, g.ny, g.nx, seed=0)
-    hist, steps, t_train = train(oslalm, torch, net, x0_tr, tg, epochs, lr, batch, log=log)
+    hist, steps, t_train = train(torch, net, x0_tr, targets, epochs, lr, batch, log=log)
     flops = 3.0 * oslalm.WarmStartNet.flops_per_image(g.ny, g.nx) * batch * steps
-    # inference net for one image at a time
+    del targets
     inf = oslalm.WarmStartNet(1, g.ny, g.nx, seed=0)
     inf.set_params(net.get_params())
 
     def cnn_init(x0):
-        return torch.clamp(inf.forward(x0.view(1, g.ny, g.nx).contiguous(), SCALE).view(1, g.ny, g.nx), min=0.0)
+        return torch.clamp(inf.forward(x0.view(1, g.ny, g.nx), SCALE), min=0.0).view(x0.shape)
 
     t0 = time.time()
-    xstars = [reference_image(oslalm, torch, geomh, wl, torch.as_tensor(y, device=dev),
-                              torch.as_tensor(w, device=dev), x0)
-              for wl, (y, w), x0 in zip(wls_te, scans_te, x0_te)]
+    xstars = run_batched(oslalm, torch, geomh, wls_te, scans_te, [x.clone() for x in x0_te], ref_schedule, chunk)
     t_ref = time.time() - t0
+    log(f"references: {t_ref:.1f} s")
     mask = fov_mask(g)
     fbp_rows = evaluate(oslalm, torch, geomh, wls_te, scans_te, x0_te, xstars, mask, None, n_eval_iter)
     cnn_rows = evaluate(oslalm, torch, geomh, wls_te, scans_te, x0_te, xstars, mask, cnn_init, n_eval_iter)
     return {
+        "geometry": {"image": [g.ny, g.nx], "views": g.nviews, "channels": g.ns, "M": M},
         "train": {"scans": n_train, "target_iterations": target_iters, "epochs": epochs, "batch": batch,
-                  "steps": steps, "seconds": t_train, "tflops": flops / t_train / 1e12,
-                  "loss_first_last": [hist[0], hist[-1]]},
+                  "steps": steps, "seconds": round(t_train, 2), "tflops_bf16": round(flops / t_train / 1e12, 2),
+                  "loss_by_epoch": [round(v, 6) for v in hist]},
+        "held_out": n_test, "reference_schedule": [list(s) for s in ref_schedule],
         "fbp_init": summarize(fbp_rows), "cnn_init": summarize(cnn_rows),
-        "held_out": n_test,
-        "seconds": {"scan_generation_cpu": t_scan, "targets_gpu": t_targets, "references_gpu": t_ref},
+        "paired": paired_gain(fbp_rows, cnn_rows),
+        "seconds": {"scan_generation_cpu": round(t_scan, 1), "targets_gpu": round(t_targets, 1),
+                    "references_gpu": round(t_ref, 1)},
     }
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--train", type=int, default=2000)
+    ap.add_argument("--test", type=int, default=100)
+    ap.add_argument("--target-iters", type=int, default=200)
+    ap.add_argument("--epochs", type=int, default=30)
+    ap.add_argument("--batch", type=int, default=8)
+    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--nx", type=int, default=512)
+    ap.add_argument("--views", type=int, default=984)
+    ap.add_argument("--channels", type=int, default=888)
+    ap.add_argument("--M", type=int, default=24)
+    ap.add_argument("--eval-iters", type=int, default=50)
+    ap.add_argument("--out", default=None)
+    a = ap.parse_args(argv)
+    res = experiment(a.train, a.test, a.target_iters, a.epochs, a.batch, a.lr, a.nx, a.views, a.channels, a.M,
+                     n_eval_iter=a.eval_iters)
+    s = json.dumps(res, indent=1)
+    if a.out:
+        with open(a.out, "w") as f:
+            f.write(s)
+    print(s)
+
+
+if __name__ == "__main__":
+    main()
