@@ -45,7 +45,7 @@ struct SliceDesc {
 struct BatchShape {
     int tx, ty, lanes;
 };
-static const BatchShape kShapes[] = {{32, 8, 4}, {16, 16, 4}, {32, 8, 8}, {16, 16, 8}, {64, 4, 2}};
+static const BatchShape kShapes[] = {{32, 8, 8}, {16, 16, 4}, {32, 8, 4}, {16, 16, 8}, {64, 4, 2}};
 constexpr int kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);
 
 __device__ __forceinline__ bool slice_active(const SliceDesc &d, int step) { return step < d.nsteps; }
@@ -138,7 +138,7 @@ __global__ void __launch_bounds__(256) batch_forward_kernel(const SliceDesc *__r
         if (valid) {
             const int lv = ray / d.geo.ns, c = ray - lv * d.geo.ns;
             const int v = __ldg(d.views + d.off[next] + lv);
-            const Ray2 rp = d.geo.rays[(size_t)v * d.geo.ns + c];
+            const RayP rp = d.geo.rays[(size_t)v * d.geo.ns + c];
             acc = march2<float>(d.geo, rp, xcur, q, LANES);
         }
 #pragma unroll
@@ -249,9 +249,9 @@ int grid_sizes(const oslalm_batch *b, int &gu, int &gf, int &gb) {
 int run_step(const oslalm_batch *b, int shape, int step, cudaStream_t st) {
     int gu, gf, gb, rc;
     switch (shape) {
-        case 0: if ((rc = grid_sizes<32, 8, 4>(b, gu, gf, gb))) return rc; return launch_step<32, 8, 4>(b, step, gu, gf, gb, st);
+        case 0: if ((rc = grid_sizes<32, 8, 8>(b, gu, gf, gb))) return rc; return launch_step<32, 8, 8>(b, step, gu, gf, gb, st);
         case 1: if ((rc = grid_sizes<16, 16, 4>(b, gu, gf, gb))) return rc; return launch_step<16, 16, 4>(b, step, gu, gf, gb, st);
-        case 2: if ((rc = grid_sizes<32, 8, 8>(b, gu, gf, gb))) return rc; return launch_step<32, 8, 8>(b, step, gu, gf, gb, st);
+        case 2: if ((rc = grid_sizes<32, 8, 4>(b, gu, gf, gb))) return rc; return launch_step<32, 8, 4>(b, step, gu, gf, gb, st);
         case 3: if ((rc = grid_sizes<16, 16, 8>(b, gu, gf, gb))) return rc; return launch_step<16, 16, 8>(b, step, gu, gf, gb, st);
         default: if ((rc = grid_sizes<64, 4, 2>(b, gu, gf, gb))) return rc; return launch_step<64, 4, 2>(b, step, gu, gf, gb, st);
     }

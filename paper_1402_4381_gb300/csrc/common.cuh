@@ -96,6 +96,19 @@ struct Geo3 {  // kernel-side cone geometry (by value)
     const View2 *views;  // [nviews]
 };
 
+// Device form of a 2D ray for the projector pair (32 bytes): the Ray2 line
+// with its integer fields as exact floats and the per-ray constants of the
+// length arithmetic precomputed once:
+//   kq    = k / 4096                  (exact)
+//   n0f   = n0                        (exact)
+//   hw    = |k / 4096 + kappa_lo / 2| (half the minor-axis width of a row,
+//                                      float32: |fma(k, 2^-12, 0.5 kappa_lo)|)
+struct __align__(16) RayP {
+    float f0, kappa_lo, lrow, kq;
+    float n0f, hw;
+    int axis, pad;
+};
+
 struct Geo2 {  // kernel-side 2D geometry (by value)
     int kind, nx, ny, ns, nviews;
     float dx, dy, xlo, ylo;  // pixel size, image lower corner (mm)
@@ -103,7 +116,8 @@ struct Geo2 {  // kernel-side 2D geometry (by value)
     float c0;                // channel coordinate of s = 0: (ns-1)/2 - offset_s
     float dso, dsd;
     float half_diag;         // pixel circumradius
-    const Ray2 *rays;        // [nviews][ns]
+    int fast_atan;           // fan beam: every pixel centre is within 45 degrees of the source's axis
+    const RayP *rays;        // [nviews][ns]
     const View2 *views;      // [nviews]
 };
 
@@ -113,7 +127,7 @@ struct oslalm_geom {
     oslalm_geom_desc d;
     int device;
     oslalm::Ray3 *d_rays3;    // 3D: [nviews][ns]
-    oslalm::Ray2 *d_rays;     // 2D: [nviews][ns]
+    oslalm::RayP *d_rays;     // 2D: [nviews][ns]
     oslalm::View2 *d_views;   // [nviews]
     oslalm::View3 *d_views3;  // 3D: [nviews]
     int *d_allviews;          // 0..nviews-1
@@ -126,54 +140,53 @@ namespace oslalm {
 bool is_3d(const oslalm_geom *g);
 
 // ---------------------------------------------------------------- chords
-// Length of a 2D ray inside pixel (ia, jb) given in the ray's (major, minor)
-// index coordinates.  Row ia (a in [ia, ia+1]) is entered through the ray's
-// position at the row centre, c = b(ia + 1/2), and the half-width |kappa|/2:
-// the row covers minor coordinates [c - |kappa|/2, c + |kappa|/2].  A row
-// that stays inside one pixel gives that pixel the full row length lrow; a
-// row that crosses pixel boundaries splits lrow by the overlaps.  The forward
-// projector (marching along a) and the gather back-projector call these same
-// functions, so both directions use bit-identical weights.
-struct RowSpan {
-    int base;       // integer minor coordinate the span is measured from
-    float lo, hi;   // minor-coordinate span of the ray inside row ia, relative to base
-};
-
+// Length of a 2D ray inside the pixels of major row ia (a in [ia, ia+1]).
+// The row is entered through the ray's minor position at the row centre,
+// c = b(ia + 1/2), and the half-width hw = |kappa|/2: the row covers minor
+// coordinates [c - hw, c + hw] (width |kappa| <= 1, so at most two pixels).
+// A row inside one pixel gives it the full row length lrow; a row crossing a
+// pixel boundary splits lrow in the ratio of the overlaps (the computed span
+// width hi - lo as the denominator, so the two parts sum to lrow).  This is
+// the exact intersection length of a straight ray with the pixels of the
+// row.  The forward projector (marching along a) and the gather
+// back-projector call this same function, so both directions use
+// bit-identical weights.
 __device__ __forceinline__ float rcp_approx(float v) {
     float r;
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
     return r;
 }
 
-__device__ __forceinline__ RowSpan row_span(const Ray2 &r, int ia) {
-    const int k = ray_k(r.packed);
-    const int p = (2 * ia + 1) * k;                 // exact: |p| < 2^24
-    const int q = p >> 12;                          // floor((ia + 1/2) k / 2048)
-    const float fr = __fmul_rn((float)(p & 4095), 2.44140625e-4f);  // exact fraction
-    const float c = __fmaf_rn((float)ia + 0.5f, r.kappa_lo, __fadd_rn(r.f0, fr));
-    const float hw = fabsf(__fmaf_rn((float)k, 2.44140625e-4f, __fmul_rn(0.5f, r.kappa_lo)));
-    RowSpan s;
-    s.base = ray_n0(r.packed) + q;
-    s.lo = __fsub_rn(c, hw);
-    s.hi = __fadd_rn(c, hw);
-    return s;
+struct RowW {
+    float j;       // minor index of the first pixel touched (exact integer)
+    float w0, w1;  // lengths in pixels j and j + 1
+};
+
+// ia2 = 2 ia + 1 and iah = ia + 1/2 as floats (exact)
+__device__ __forceinline__ RowW row_weights(const RayP &r, float ia2, float iah) {
+    const float pq = __fmul_rn(ia2, r.kq);  // (2 ia + 1) k / 4096: exact, |(2 ia + 1) k| < 2^24
+    const float q = floorf(pq);
+    const float fr = __fsub_rn(pq, q);      // exact fraction
+    const float c = __fmaf_rn(iah, r.kappa_lo, __fadd_rn(r.f0, fr));  // relative to n0 + q
+    const float lo = __fsub_rn(c, r.hw), hi = __fadd_rn(c, r.hw);
+    const float jl = floorf(lo), jh = floorf(hi);
+    const float jl1 = __fadd_rn(jl, 1.f);
+    RowW w;
+    w.j = __fadd_rn(__fadd_rn(r.n0f, q), jl);
+    const bool split = jl != jh;
+    const float scale = __fmul_rn(r.lrow, rcp_approx(__fsub_rn(hi, lo)));
+    w.w0 = split ? __fmul_rn(__fsub_rn(jl1, lo), scale) : r.lrow;
+    w.w1 = split ? __fmul_rn(__fsub_rn(fminf(hi, __fadd_rn(jl1, 1.f)), jl1), scale) : 0.f;
+    return w;
 }
 
-// length of the row inside minor pixel jj (relative to the span's base)
-__device__ __forceinline__ float row_chord(const RowSpan &s, float lrow, float jj) {
-    const float jl = floorf(s.lo), jh = floorf(s.hi);
-    if (jl == jh) return jj == jl ? lrow : 0.f;
-    const float scale = __fmul_rn(lrow, rcp_approx(__fsub_rn(s.hi, s.lo)));
-    const float ov = __fsub_rn(fminf(s.hi, jj + 1.f), fmaxf(s.lo, jj));
-    return ov > 0.f ? __fmul_rn(ov, scale) : 0.f;
-}
-
-__device__ __forceinline__ float chord2(const Ray2 &r, int ix, int iy) {
-    const int axis = ray_axis(r.packed);
-    const int ia = axis ? iy : ix;
-    const int jb = axis ? ix : iy;
-    RowSpan s = row_span(r, ia);
-    return row_chord(s, r.lrow, (float)(jb - s.base));
+// length of ray r in pixel (ix, iy)
+__device__ __forceinline__ float chord2(const RayP &r, float ixf, float iyf) {
+    const float ia = r.axis ? iyf : ixf;
+    const float jb = r.axis ? ixf : iyf;
+    const RowW w = row_weights(r, __fmaf_rn(2.f, ia, 1.f), __fadd_rn(ia, 0.5f));
+    const float d = __fsub_rn(jb, w.j);
+    return d == 0.f ? w.w0 : (d == 1.f ? w.w1 : 0.f);
 }
 
 // ---------------------------------------------------------------- projector launchers

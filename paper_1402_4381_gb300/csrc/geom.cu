@@ -81,6 +81,22 @@ static Ray2 make_ray2(const oslalm_geom_desc &d, double px, double py, double ux
     return r;
 }
 
+// Device form of a 2D ray: integer fields as exact floats and the row
+// half-width in float32 (fmaf is correctly rounded on every host).
+static RayP make_rayp(const Ray2 &r) {
+    RayP o;
+    const int k = ray_k(r.packed);
+    o.f0 = r.f0;
+    o.kappa_lo = r.kappa_lo;
+    o.lrow = r.lrow;
+    o.kq = (float)k * 2.44140625e-4f;
+    o.n0f = (float)ray_n0(r.packed);
+    o.hw = fabsf(fmaf((float)k, 2.44140625e-4f, 0.5f * r.kappa_lo));
+    o.axis = ray_axis(r.packed);
+    o.pad = 0;
+    return o;
+}
+
 // 2D ray parameters of every channel of view v (FP64 set-up).
 static void ray_table_view(const oslalm_geom_desc &d, int v, Ray2 *out) {
     double cu, su;
@@ -212,6 +228,15 @@ oslalm::Geo2 oslalm_geom::geo2() const {
     o.dso = (float)d.dso;
     o.dsd = (float)d.dsd;
     o.half_diag = (float)(0.5 * sqrt(d.dx * d.dx + d.dy * d.dy));
+    // |b| <= a at every pixel centre when the image's corners stay within
+    // dso / sqrt(2) of the rotation centre
+    double rc = 0.0;
+    for (int cx = -1; cx <= 1; cx += 2)
+        for (int cy = -1; cy <= 1; cy += 2) {
+            double ex = d.offset_x + cx * 0.5 * d.nx * d.dx, ey = d.offset_y + cy * 0.5 * d.ny * d.dy;
+            rc = fmax(rc, sqrt(ex * ex + ey * ey));
+        }
+    o.fast_atan = d.kind == OSLALM_FAN2D_ARC && rc < 0.99 * d.dso / sqrt(2.0);
     o.rays = d_rays;
     o.views = d_views;
     return o;
@@ -256,8 +281,9 @@ int oslalm_geom_create(const oslalm_geom_desc *desc, oslalm_geom **out) {
     std::vector<View2> views(d.nviews);
     std::vector<View3> views3(d.nviews);
     std::vector<int> allv(d.nviews);
-    std::vector<Ray2> rays;
+    std::vector<RayP> rays;
     std::vector<Ray3> rays3;
+    std::vector<Ray2> rview(d.ns);
     bool two_d = d.kind != OSLALM_CONE3D_FLAT;
     if (two_d) rays.resize((size_t)d.nviews * d.ns);
     else rays3.resize((size_t)d.nviews * d.ns);
@@ -267,7 +293,10 @@ int oslalm_geom_create(const oslalm_geom_desc *desc, oslalm_geom **out) {
         views[v] = View2{(float)cu, (float)su, 0.f, 0.f};
         views3[v] = View3{(float)cu, (float)su, (float)(-d.dso * cu), (float)(-d.dso * su)};
         allv[v] = v;
-        if (two_d) ray_table_view(d, v, &rays[(size_t)v * d.ns]);
+        if (two_d) {
+            ray_table_view(d, v, rview.data());
+            for (int c = 0; c < d.ns; ++c) rays[(size_t)v * d.ns + c] = make_rayp(rview[c]);
+        }
         else ray3_table_view(d, v, &rays3[(size_t)v * d.ns]);
     }
     auto cleanup = [&](int code, const char *what, cudaError_t e) {
@@ -279,12 +308,12 @@ int oslalm_geom_create(const oslalm_geom_desc *desc, oslalm_geom **out) {
     if ((e = cudaMalloc(&g->d_views, sizeof(View2) * d.nviews)) != cudaSuccess) return cleanup(OSLALM_ERR_ALLOC, "cudaMalloc views", e);
     if ((e = cudaMalloc(&g->d_views3, sizeof(View3) * d.nviews)) != cudaSuccess) return cleanup(OSLALM_ERR_ALLOC, "cudaMalloc views3", e);
     if ((e = cudaMalloc(&g->d_allviews, sizeof(int) * d.nviews)) != cudaSuccess) return cleanup(OSLALM_ERR_ALLOC, "cudaMalloc views", e);
-    if (two_d && (e = cudaMalloc(&g->d_rays, sizeof(Ray2) * rays.size())) != cudaSuccess) return cleanup(OSLALM_ERR_ALLOC, "cudaMalloc rays", e);
+    if (two_d && (e = cudaMalloc(&g->d_rays, sizeof(RayP) * rays.size())) != cudaSuccess) return cleanup(OSLALM_ERR_ALLOC, "cudaMalloc rays", e);
     if (!two_d && (e = cudaMalloc(&g->d_rays3, sizeof(Ray3) * rays3.size())) != cudaSuccess) return cleanup(OSLALM_ERR_ALLOC, "cudaMalloc rays3", e);
     if ((e = cudaMemcpy(g->d_views, views.data(), sizeof(View2) * d.nviews, cudaMemcpyHostToDevice)) != cudaSuccess) return cleanup(OSLALM_ERR_CUDA, "upload", e);
     if ((e = cudaMemcpy(g->d_views3, views3.data(), sizeof(View3) * d.nviews, cudaMemcpyHostToDevice)) != cudaSuccess) return cleanup(OSLALM_ERR_CUDA, "upload", e);
     if ((e = cudaMemcpy(g->d_allviews, allv.data(), sizeof(int) * d.nviews, cudaMemcpyHostToDevice)) != cudaSuccess) return cleanup(OSLALM_ERR_CUDA, "upload", e);
-    if (two_d && (e = cudaMemcpy(g->d_rays, rays.data(), sizeof(Ray2) * rays.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return cleanup(OSLALM_ERR_CUDA, "upload", e);
+    if (two_d && (e = cudaMemcpy(g->d_rays, rays.data(), sizeof(RayP) * rays.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return cleanup(OSLALM_ERR_CUDA, "upload", e);
     if (!two_d && (e = cudaMemcpy(g->d_rays3, rays3.data(), sizeof(Ray3) * rays3.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return cleanup(OSLALM_ERR_CUDA, "upload", e);
     *out = g;
     return OSLALM_OK;

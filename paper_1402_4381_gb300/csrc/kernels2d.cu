@@ -22,8 +22,8 @@
 namespace oslalm {
 
 // ---------------------------------------------------------------- forward
-// One warp = 8 rays (adjacent channels) x 4 lanes; lane q of a ray takes
-// rows ia0+q, ia0+q+4, ...; the 4 partial sums are combined by shuffles in a
+// One warp = 4 rays (adjacent channels) x 8 lanes; lane q of a ray takes
+// rows ia0+q, ia0+q+8, ...; the 8 partial sums are combined by shuffles in a
 // fixed order.
 template <int MODE, typename WT>
 __global__ void __launch_bounds__(128) fp2d_kernel(Geo2 g, const float *__restrict__ x, float *__restrict__ out,
@@ -31,8 +31,8 @@ __global__ void __launch_bounds__(128) fp2d_kernel(Geo2 g, const float *__restri
                                                    const float *__restrict__ y, const WT *__restrict__ w,
                                                    const float *__restrict__ wscale, float gain) {
     const int lane = threadIdx.x & 31;
-    const int q = lane >> 3;
-    const int ray = (blockIdx.x * 4 + (threadIdx.x >> 5)) * 8 + (lane & 7);
+    const int q = lane >> 2;
+    const int ray = (blockIdx.x * 4 + (threadIdx.x >> 5)) * 4 + (lane & 3);
     const bool valid = ray < nv * g.ns;
     float acc = 0.f;
     int lv = 0, c = 0, v = -1;
@@ -41,10 +41,11 @@ __global__ void __launch_bounds__(128) fp2d_kernel(Geo2 g, const float *__restri
         c = ray - lv * g.ns;
         v = __ldg(views + lv);
         if ((unsigned)v < (unsigned)g.nviews) {
-            const Ray2 rp = g.rays[(size_t)v * g.ns + c];
-            acc = march2<float>(g, rp, x, q, 4);
+            const RayP rp = g.rays[(size_t)v * g.ns + c];
+            acc = march2<float>(g, rp, x, q, 8);
         }
     }
+    acc += __shfl_xor_sync(0xffffffffu, acc, 4);
     acc += __shfl_xor_sync(0xffffffffu, acc, 8);
     acc += __shfl_xor_sync(0xffffffffu, acc, 16);
     if (!valid || q != 0) return;
@@ -81,38 +82,59 @@ __global__ void __launch_bounds__(128) cost2d_kernel(Geo2 g, const float *__rest
 }
 
 // ---------------------------------------------------------------- back-projection
+// Block of 8 warps over a 32 x 4 pixel tile: warp w takes view group w % 4
+// for pixel rows w / 4 and w / 4 + 2 (two independent chains per thread);
+// the group partials meet in shared memory and are added in group order.
+template <int MODE>
+__device__ __forceinline__ double bp2d_epilogue(const UpdateArgs &ua, float *out, size_t p, float acc) {
+    if (MODE == BP_STORE) {
+        out[p] = acc;
+    } else if (MODE == BP_ACCUM) {
+        out[p] += acc;
+    } else if (MODE == BP_INIT) {
+        ua.zeta[p] = acc;
+        ua.g[p] = acc;
+    } else {
+        // split-gradient update and restart indicator (old g, old zeta)
+        const double rho = ua.state->rho;
+        const float a = (float)(rho / (rho + 1.0));
+        const float b = (float)(1.0 / (rho + 1.0));
+        const float z_old = ua.zeta[p];
+        const float g_old = ua.g[p];
+        ua.zeta[p] = acc;
+        ua.g[p] = a * acc + b * g_old;
+        return (double)(g_old - acc) * (double)(acc - z_old);
+    }
+    return 0.0;
+}
+
 template <int MODE>
 __global__ void __launch_bounds__(256) bp2d_kernel(Geo2 g, const float *__restrict__ r, float *__restrict__ out,
                                                    const int *__restrict__ views, int nv, UpdateArgs ua) {
-    const int ix = blockIdx.x * 32 + threadIdx.x;
-    const int iy = blockIdx.y * 8 + threadIdx.y;
-    const bool valid = ix < g.nx && iy < g.ny;
-    const float acc = valid ? bp_pixel_sum(g, r, views, nv, ix, iy) : 0.f;
-    const size_t p = (size_t)iy * g.nx + ix;
-    if (MODE == BP_STORE) {
-        if (valid) out[p] = acc;
-    } else if (MODE == BP_ACCUM) {
-        if (valid) out[p] += acc;
-    } else if (MODE == BP_INIT) {
-        if (valid) {
-            ua.zeta[p] = acc;
-            ua.g[p] = acc;
+    __shared__ float part[kBpGroups][4][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int grp = warp & 3, row = warp >> 2;
+    const int ix = blockIdx.x * 32 + lane;
+    const int iy0 = blockIdx.y * 4 + row, iy1 = iy0 + 2;
+    float a = 0.f, b = 0.f;
+    if (ix < g.nx && iy0 < g.ny)
+        bp_pixel_range2(g, r, views, bp_group_begin(nv, grp), bp_group_begin(nv, grp + 1), ix, iy0, iy1, iy1 < g.ny,
+                        a, b);
+    part[grp][row][lane] = a;
+    part[grp][row + 2][lane] = b;
+    __syncthreads();
+    double xi_local = 0.0;
+    if (threadIdx.x < 128) {
+        const int pr = threadIdx.x >> 5;
+        const int px = blockIdx.x * 32 + lane, py = blockIdx.y * 4 + pr;
+        if (px < g.nx && py < g.ny) {
+            float acc = 0.f;
+#pragma unroll
+            for (int k = 0; k < kBpGroups; ++k) acc += part[k][pr][lane];
+            xi_local = bp2d_epilogue<MODE>(ua, out, (size_t)py * g.nx + px, acc);
         }
-    } else {
-        // split-gradient update and restart indicator (old g, old zeta)
-        double xi_local = 0.0;
-        if (valid) {
-            const double rho = ua.state->rho;
-            const float a = (float)(rho / (rho + 1.0));
-            const float b = (float)(1.0 / (rho + 1.0));
-            const float z_old = ua.zeta[p];
-            const float g_old = ua.g[p];
-            ua.zeta[p] = acc;
-            ua.g[p] = a * acc + b * g_old;
-            xi_local = (double)(g_old - acc) * (double)(acc - z_old);
-        }
-        subset_iteration_epilogue(ua, xi_local);
     }
+    if (MODE == BP_UPDATE) subset_iteration_epilogue(ua, xi_local);
 }
 
 // ---------------------------------------------------------------- update
@@ -153,13 +175,13 @@ __global__ void __launch_bounds__(256) reg_value2d_kernel(int nx, int ny, const 
 }
 
 // ---------------------------------------------------------------- launchers
-int bp2d_blocks(const Geo2 &g) { return ((g.nx + 31) / 32) * ((g.ny + 7) / 8); }
+int bp2d_blocks(const Geo2 &g) { return ((g.nx + 31) / 32) * ((g.ny + 3) / 4); }
 
 template <int MODE>
 static int launch_fp2d_t(const Geo2 &g, const float *x, float *out, const int *views, int nv, const float *y,
                          WeightRef w, float gain, cudaStream_t st) {
     const int n = nv * g.ns;
-    const int grid = (n + 31) / 32;  // 32 rays per 128-thread block
+    const int grid = (n + 15) / 16;  // 16 rays per 128-thread block
     if (MODE == FP_PLAIN || w.dtype == OSLALM_F32)
         fp2d_kernel<MODE, float><<<grid, 128, 0, st>>>(g, x, out, views, nv, y, (const float *)w.ptr, w.scale, gain);
     else if (w.dtype == OSLALM_F16)
@@ -180,7 +202,7 @@ int launch_fp2d(const Geo2 &g, const float *x, float *out, const int *views, int
 
 int launch_bp2d(const Geo2 &g, const float *r, float *out, const int *views, int nv, int mode, const UpdateArgs *ua,
                 cudaStream_t st) {
-    dim3 block(32, 8), grid((g.nx + 31) / 32, (g.ny + 7) / 8);
+    dim3 block(256), grid((g.nx + 31) / 32, (g.ny + 3) / 4);
     UpdateArgs a{};
     if (ua) a = *ua;
     switch (mode) {

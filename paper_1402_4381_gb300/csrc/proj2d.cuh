@@ -9,9 +9,8 @@
 namespace oslalm {
 
 // Major-axis rows [ia0, ia1] whose minor span can meet [0, Nb) (conservative).
-__device__ __forceinline__ void ray_rows(const Geo2 &g, const Ray2 &rp, int &ia0, int &ia1) {
-    const int axis = ray_axis(rp.packed);
-    const int n0 = ray_n0(rp.packed);
+__device__ __forceinline__ void ray_rows(const Geo2 &g, const RayP &rp, int &ia0, int &ia1) {
+    const int axis = rp.axis;
     const int Na = axis ? g.ny : g.nx;
     const int Nb = axis ? g.nx : g.ny;
     ia0 = 0;
@@ -20,93 +19,178 @@ __device__ __forceinline__ void ray_rows(const Geo2 &g, const Ray2 &rp, int &ia0
         ia1 = -1;
         return;
     }
-    const float kap = (float)ray_k(rp.packed) * 4.8828125e-4f + rp.kappa_lo;
+    const float kap = __fadd_rn(__fadd_rn(rp.kq, rp.kq), rp.kappa_lo);
     if (kap != 0.f) {
         // b - n0 in [-1, Nb - n0 + 1] at the row ends, with a row of margin
-        float t0 = ((float)(-n0) - 1.f - rp.f0) / kap;
-        float t1 = ((float)(Nb - n0) + 1.f - rp.f0) / kap;
+        float t0 = (-rp.n0f - 1.f - rp.f0) / kap;
+        float t1 = ((float)Nb - rp.n0f + 1.f - rp.f0) / kap;
         float tlo = fmaxf(fminf(t0, t1), -2.f), thi = fminf(fmaxf(t0, t1), (float)Na + 2.f);
         ia0 = max(0, (int)floorf(tlo) - 1);
         ia1 = min(Na - 1, (int)ceilf(thi) + 1);
     } else {
-        int j = n0 + (int)floorf(rp.f0);
+        int j = (int)rp.n0f + (int)floorf(rp.f0);
         if (j < 0 || j >= Nb) ia1 = -1;
     }
 }
 
-// Sum of chord x pixel over rows first, first+stride, ... of the ray.
+// Sum of length x pixel over rows first, first+stride, ... of the ray (each
+// row adds its first pixel, then its second).
 template <typename ACC>
-__device__ __forceinline__ ACC march2(const Geo2 &g, const Ray2 &rp, const float *__restrict__ x, int first,
+__device__ __forceinline__ ACC march2(const Geo2 &g, const RayP &rp, const float *__restrict__ x, int first,
                                       int stride) {
-    const int axis = ray_axis(rp.packed);
+    const int axis = rp.axis;
     const int Nb = axis ? g.nx : g.ny;
     const int sa = axis ? g.nx : 1;
     const int sb = axis ? 1 : g.nx;
     int ia0, ia1;
     ray_rows(g, rp, ia0, ia1);
     ACC acc = 0;
-    for (int ia = ia0 + first; ia <= ia1; ia += stride) {
-        const RowSpan s = row_span(rp, ia);
-        const float jlo = floorf(s.lo), jhi = floorf(s.hi);
-        if (jlo == jhi) {  // the row stays inside one pixel: full row length
-            const int j = s.base + (int)jlo;
-            if ((unsigned)j < (unsigned)Nb) acc += (ACC)rp.lrow * (ACC)__ldg(x + (size_t)ia * sa + (size_t)j * sb);
-            continue;
-        }
-        for (float jj = jlo; jj <= jhi; jj += 1.f) {
-            const int j = s.base + (int)jj;
-            if ((unsigned)j < (unsigned)Nb) {
-                const float ch = row_chord(s, rp.lrow, jj);
-                acc += (ACC)ch * (ACC)__ldg(x + (size_t)ia * sa + (size_t)j * sb);
-            }
-        }
+    int ia = ia0 + first;
+    float ia2 = (float)(2 * ia + 1), iah = (float)ia + 0.5f;
+    const float d2 = (float)(2 * stride), d1 = (float)stride;
+#pragma unroll 2
+    for (; ia <= ia1; ia += stride, ia2 += d2, iah += d1) {
+        const RowW w = row_weights(rp, ia2, iah);
+        const int j = (int)w.j;
+        const float *row = x + (size_t)ia * sa;
+        const float x0 = (unsigned)j < (unsigned)Nb ? __ldg(row + (ptrdiff_t)j * sb) : 0.f;
+        const float x1 = (w.w1 != 0.f && (unsigned)(j + 1) < (unsigned)Nb) ? __ldg(row + (ptrdiff_t)(j + 1) * sb) : 0.f;
+        acc = fma((ACC)w.w0, (ACC)x0, acc);
+        acc = fma((ACC)w.w1, (ACC)x1, acc);
     }
     return acc;
 }
 
+// atan(t) for |t| <= 1: t P(t^2), P of degree 5 fitted by least squares at
+// Chebyshev nodes of [0, 1] (max error 1.9e-6 in float32 arithmetic)
+__device__ __forceinline__ float atan_unit(float t) {
+    const float s = t * t;
+    float p = -1.146580931e-02f;
+    p = fmaf(p, s, 5.195053294e-02f);
+    p = fmaf(p, s, -1.157294437e-01f);
+    p = fmaf(p, s, 1.932352930e-01f);
+    p = fmaf(p, s, -3.325683177e-01f);
+    p = fmaf(p, s, 9.999744892e-01f);
+    return p * t;
+}
+
 // channel window of pixel centre (px, py) in view vw: channels whose ray may
 // cross the pixel, widened by a margin far above the rounding of the ray
-// tables so that no channel with a non-zero chord is missed.
+// tables and the error of the angle evaluation, so that no channel with a
+// non-zero length is missed.
 __device__ __forceinline__ void channel_window(const Geo2 &g, const View2 &vw, float px, float py, int &c0,
                                                int &c1) {
-    constexpr float kMargin = 0.02f;
     float cc, hw;
     if (g.kind == OSLALM_PAR2D) {
+        constexpr float kMargin = 0.02f;
         float s = -px * vw.su + py * vw.cu;
         cc = s * g.inv_ds + g.c0;
-        hw = 0.5f * (g.dx * fabsf(vw.su) + g.dy * fabsf(vw.cu)) * g.inv_ds;
+        hw = 0.5f * (g.dx * fabsf(vw.su) + g.dy * fabsf(vw.cu)) * g.inv_ds + kMargin;
     } else {
         float a = px * vw.cu + py * vw.su + g.dso;  // along u from the source
         float b = -px * vw.su + py * vw.cu;         // along e
-        float gam = atan2f(b, a);
+        // fast form when |b| <= a for every pixel: angle error < 2.5e-6 rad
+        const float gam = g.fast_atan ? atan_unit(__fdividef(b, a)) : atan2f(b, a);
+        const float kMargin = 0.02f + 2.5e-6f * g.dsd * g.inv_ds;
         float d2 = a * a + b * b - g.half_diag * g.half_diag;
         float ang = g.half_diag * rsqrtf(fmaxf(d2, 1e-12f));  // >= angular radius of the pixel
         cc = gam * g.dsd * g.inv_ds + g.c0;
-        hw = ang * 1.0001f * g.dsd * g.inv_ds;
+        hw = ang * 1.0001f * g.dsd * g.inv_ds + kMargin;
     }
-    c0 = max(0, (int)ceilf(cc - hw - kMargin));
-    c1 = min(g.ns - 1, (int)floorf(cc + hw + kMargin));
+    c0 = max(0, (int)ceilf(cc - hw));
+    c1 = min(g.ns - 1, (int)floorf(cc + hw));
 }
 
-// Sum over the listed views of chord x r for the rays crossing pixel (ix, iy).
-__device__ __forceinline__ float bp_pixel_sum(const Geo2 &g, const float *__restrict__ r,
-                                              const int *__restrict__ views, int nv, int ix, int iy) {
+// pixel indices as exact floats for the length arithmetic
+struct PixF {
+    float x2, xh, xf, y2, yh, yf;  // 2 i + 1, i + 1/2, i for i = ix, iy
+};
+
+__device__ __forceinline__ PixF pix_f(int ix, int iy) {
+    PixF p;
+    p.xf = (float)ix;
+    p.yf = (float)iy;
+    p.x2 = __fmaf_rn(2.f, p.xf, 1.f);
+    p.y2 = __fmaf_rn(2.f, p.yf, 1.f);
+    p.xh = __fadd_rn(p.xf, 0.5f);
+    p.yh = __fadd_rn(p.yf, 0.5f);
+    return p;
+}
+
+// length of ray r in the pixel (same arithmetic as chord2)
+__device__ __forceinline__ float chord_px(const RayP &r, const PixF &p) {
+    const bool ay = r.axis != 0;
+    const RowW w = row_weights(r, ay ? p.y2 : p.x2, ay ? p.yh : p.xh);
+    const float d = __fsub_rn(ay ? p.xf : p.yf, w.j);
+    return d == 0.f ? w.w0 : (d == 1.f ? w.w1 : 0.f);
+}
+
+// The back-projected value of a pixel is summed in kBpGroups consecutive
+// view groups [begin(k), begin(k+1)): each group's partial in view order
+// (channels ascending within a view), then the partials in group order.  The
+// single-problem kernel gives the groups to different warps; the batched
+// kernel sums them in one thread; both give the same bits.
+constexpr int kBpGroups = 4;
+__device__ __forceinline__ int bp_group_begin(int nv, int k) { return (nv * k) / kBpGroups; }
+
+// Sum over views [lv0, lv1) of length x r for pixels (ix, iy0) and (ix, iy1)
+// (two independent chains; has1 = false: only the first pixel).
+__device__ __forceinline__ void bp_pixel_range2(const Geo2 &g, const float *__restrict__ r,
+                                                const int *__restrict__ views, int lv0, int lv1, int ix, int iy0,
+                                                int iy1, bool has1, float &acc0, float &acc1) {
+    acc0 = 0.f;
+    acc1 = 0.f;
+    const float px = g.xlo + ((float)ix + 0.5f) * g.dx;
+    const float py0 = g.ylo + ((float)iy0 + 0.5f) * g.dy;
+    const float py1 = g.ylo + ((float)iy1 + 0.5f) * g.dy;
+    const PixF pf0 = pix_f(ix, iy0), pf1 = pix_f(ix, iy1);
+    for (int lv = lv0; lv < lv1; ++lv) {
+        const int v = __ldg(views + lv);
+        if ((unsigned)v >= (unsigned)g.nviews) continue;  // caller-supplied view out of range
+        const View2 vw = g.views[v];
+        int a0, a1, b0, b1;
+        channel_window(g, vw, px, py0, a0, a1);
+        channel_window(g, vw, px, py1, b0, b1);
+        if (!has1) b1 = b0 - 1;
+        const RayP *rr = g.rays + (size_t)v * g.ns;
+        const float *rv = r + (size_t)lv * g.ns;
+        const int n = max(a1 - a0, b1 - b0) + 1;
+        for (int k = 0; k < n; ++k) {
+            const int ca = a0 + k, cb = b0 + k;
+            if (ca <= a1) acc0 = fmaf(chord_px(rr[ca], pf0), __ldg(rv + ca), acc0);
+            if (cb <= b1) acc1 = fmaf(chord_px(rr[cb], pf1), __ldg(rv + cb), acc1);
+        }
+    }
+}
+
+// Sum over views [lv0, lv1) of length x r for the rays crossing pixel (ix, iy).
+__device__ __forceinline__ float bp_pixel_range(const Geo2 &g, const float *__restrict__ r,
+                                                const int *__restrict__ views, int lv0, int lv1, int ix, int iy) {
     float acc = 0.f;
     const float px = g.xlo + ((float)ix + 0.5f) * g.dx;
     const float py = g.ylo + ((float)iy + 0.5f) * g.dy;
-    for (int lv = 0; lv < nv; ++lv) {
+    const PixF pf = pix_f(ix, iy);
+    for (int lv = lv0; lv < lv1; ++lv) {
         const int v = __ldg(views + lv);
         if ((unsigned)v >= (unsigned)g.nviews) continue;  // caller-supplied view out of range
         const View2 vw = g.views[v];
         int c0, c1;
         channel_window(g, vw, px, py, c0, c1);
-        const Ray2 *rr = g.rays + (size_t)v * g.ns;
+        const RayP *rr = g.rays + (size_t)v * g.ns;
         const float *rv = r + (size_t)lv * g.ns;
-        for (int c = c0; c <= c1; ++c) {
-            const Ray2 rp = rr[c];
-            acc = fmaf(chord2(rp, ix, iy), __ldg(rv + c), acc);
-        }
+#pragma unroll 2
+        for (int c = c0; c <= c1; ++c) acc = fmaf(chord_px(rr[c], pf), __ldg(rv + c), acc);
     }
+    return acc;
+}
+
+// A'r at pixel (ix, iy) over the listed views, in the grouped order above.
+__device__ __forceinline__ float bp_pixel_sum(const Geo2 &g, const float *__restrict__ r,
+                                              const int *__restrict__ views, int nv, int ix, int iy) {
+    float acc = 0.f;
+#pragma unroll
+    for (int k = 0; k < kBpGroups; ++k)
+        acc += bp_pixel_range(g, r, views, bp_group_begin(nv, k), bp_group_begin(nv, k + 1), ix, iy);
     return acc;
 }
 

@@ -36,26 +36,33 @@ def _fma32(a, b, c):
 
 def chords_float32(tab, c, ia, jb):
     """Length of ray c inside pixels (ia, jb) (major, minor indices), with the
-    float32 operations of the device code in the same order (the device's
+    float32 operations of the device code in the same order: the device
+    table's derived constants (k / 4096, n0, the row half-width hw), then the
+    row-centre span and the two-pixel split of each row (the device's
     approximate reciprocal is replaced by an exact one here)."""
     f0, kl, lrow = F(tab["f0"][c]), F(tab["kappa_lo"][c]), F(tab["lrow"][c])
     axis, n0, k = decode(tab["packed"][c:c + 1])
     n0, k = int(n0[0]), int(k[0])
-    ia = ia.astype(np.int32)
-    p = (2 * ia + 1) * np.int32(k)
-    q = p >> 12
-    fr = ((p & 4095).astype(F) * F(2.0 ** -12)).astype(F)
-    cc = _fma32(ia.astype(F) + F(0.5), kl, (f0 + fr).astype(F))
-    hw = np.abs(_fma32(F(k), F(2.0 ** -12), (F(0.5) * kl).astype(F)))
+    kq = F(F(k) * F(2.0 ** -12))
+    hw = np.abs(_fma32(F(k), F(2.0 ** -12), F(F(0.5) * kl)))
+    ia = np.asarray(ia, np.int64)
+    ia2 = (2 * ia + 1).astype(F)
+    iah = (ia.astype(F) + F(0.5)).astype(F)
+    pq = (ia2 * kq).astype(F)
+    q = np.floor(pq)
+    fr = (pq - q).astype(F)
+    cc = _fma32(iah, kl, (f0 + fr).astype(F))
     lo, hi = (cc - hw).astype(F), (cc + hw).astype(F)
-    base = n0 + q
-    jj = (jb - base).astype(F)
     jl, jh = np.floor(lo), np.floor(hi)
+    jl1 = (jl + F(1)).astype(F)
+    j = (F(n0) + q).astype(F) + jl
+    split = jl != jh
     with np.errstate(divide="ignore", invalid="ignore"):
         scale = (lrow * (F(1) / (hi - lo).astype(F))).astype(F)
-    ov = (np.minimum(hi, jj + F(1)) - np.maximum(lo, jj)).astype(F)
-    split = np.where(ov > 0, (ov * scale).astype(F), F(0))
-    ch = np.where(jl == jh, np.where(jj == jl, lrow, F(0)), split)
+    w0 = np.where(split, ((jl1 - lo).astype(F) * scale).astype(F), lrow)
+    w1 = np.where(split, ((np.minimum(hi, (jl1 + F(1)).astype(F)) - jl1).astype(F) * scale).astype(F), F(0))
+    d = np.asarray(jb, np.int64).astype(F) - j
+    ch = np.where(d == 0, w0, np.where(d == 1, w1, F(0)))
     return ch.astype(np.float64), int(axis[0])
 
 
