@@ -95,7 +95,11 @@ typedef struct oslalm_params {
     int nbr;          /* 4 or 8 (2D); 6 or 26 (3D); w_jk = 1/index distance */
     int M;            /* number of ordered subsets (views v with v mod M = m) */
     double rho_min;   /* continuation floor (Sec. III-B uses 1e-3) */
-    int n_inner;      /* inner FISTA steps of the constrained denoising; 1 */
+    int n_inner;      /* FISTA steps (1..64) on the constrained denoising problem of the
+                         x-update (Sec. IV-A) from the previous image, each a projected
+                         SQS step from the extrapolated point with denominators
+                         rho D + D_R(v); 1 = the single projected SQS step.  Batches
+                         (oslalm_batch_*) take n_inner = 1 only. */
     int rho_mode;     /* OSLALM_RHO_* */
     double rho_fixed; /* rho for OSLALM_RHO_FIXED */
     int curvature;    /* OSLALM_CURV_* */

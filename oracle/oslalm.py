@@ -228,13 +228,26 @@ def ct_subset_data(geom, y, w, M, projector):
 # --------------------------------------------------------------------------
 
 
+def fista_momentum(n: int):
+    """FISTA (Beck & Teboulle 2009) momentum weights gamma_i = (tau_i - 1) /
+    tau_{i+1}, tau_0 = 1, tau_{i+1} = (1 + sqrt(1 + 4 tau_i^2)) / 2, for the
+    inner steps i = 0..n-1 (gamma_0 = 0)."""
+    tau, out = 1.0, []
+    for _ in range(n):
+        tn = 0.5 * (1.0 + math.sqrt(1.0 + 4.0 * tau * tau))
+        out.append((tau - 1.0) / tn)
+        tau = tn
+    return out
+
+
 class OsLalm:
-    """OS-LALM with n = 1 inner step, fixed rho or downward continuation."""
+    """OS-LALM with n inner FISTA steps (n = 1: one projected SQS step),
+    fixed rho or downward continuation."""
 
     def __init__(self, data: SubsetData, D, beta: float, delta: float, nbr: int,
                  order: Optional[Sequence[int]] = None, rho_mode: str = "continuation",
                  rho_fixed: float = 1.0, rho_min: float = 1e-3, curvature: str = "huber",
-                 nonneg: bool = True, replay: Optional[Sequence[int]] = None):
+                 nonneg: bool = True, replay: Optional[Sequence[int]] = None, n_inner: int = 1):
         self.data = data
         self.M = data.M
         self.D = np.asarray(D, dtype=np.float64)
@@ -246,6 +259,7 @@ class OsLalm:
         self.curvature = curvature
         self.nonneg = nonneg
         self.replay = replay
+        self.n_inner = int(n_inner)
         self.history = []
 
     def init(self, x0):
@@ -262,14 +276,37 @@ class OsLalm:
         return (reg_grad(x, self.beta, self.delta, self.nbr),
                 reg_curv(x, self.beta, self.delta, self.nbr, self.curvature))
 
+    def inner(self, x, s, rho):
+        """The x-update of Eq. os_lalm_iterates with h = R + iota_Omega (Sec.
+        IV-A): the constrained denoising problem
+            min_{v in Omega}  Phi(v) = R(v) + (rho/2) ||v - x + D^-1 s / rho||_D^2
+        by n FISTA steps from the warm start x.  Step i takes a projected
+        separable-quadratic-surrogate step from the extrapolated point v_i
+        with the denominators rho D + D_R(v_i):
+            u_{i+1} = P_Omega(v_i - grad Phi(v_i) / (rho D + D_R(v_i))),
+            grad Phi(v) = grad R(v) + s + rho D (v - x),
+            v_{i+1} = u_{i+1} + gamma_i (u_{i+1} - u_i),  u_0 = v_0 = x,
+        and returns u_n.  n = 1 is the single projected step
+        x - (s + grad R(x)) / (rho D + D_R(x))."""
+        gam = fista_momentum(self.n_inner)
+        u_prev, v = x, x
+        for i in range(self.n_inner):
+            gR, DR = self._reg(v)
+            if i == 0:
+                u = x - (s + gR) / (rho * self.D + DR)
+            else:
+                u = v - (gR + s + rho * self.D * (v - x)) / (rho * self.D + DR)
+            if self.nonneg:
+                u = np.maximum(u, 0.0)
+            v = u + gam[i] * (u - u_prev)
+            u_prev = u
+        return u_prev
+
     def step(self):
         rho, x, g, zeta = self.rho, self.x, self.g, self.zeta
-        # search direction and the inner step (n = 1)
+        # search direction and the inner constrained denoising (n steps)
         s = rho * zeta + (1.0 - rho) * g
-        gR, DR = self._reg(x)
-        x_new = x - (s + gR) / (rho * self.D + DR)
-        if self.nonneg:
-            x_new = np.maximum(x_new, 0.0)
+        x_new = self.inner(x, s, rho)
         # next subset gradient and split-gradient update
         m_next = self.order[(self.j + 1) % self.M]
         zeta_new = self.data.grad_subset(x_new, m_next)

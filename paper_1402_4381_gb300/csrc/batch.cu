@@ -315,6 +315,7 @@ int oslalm_batch_create(oslalm_problem *const *probs, int n, oslalm_batch **out)
         if (!p) return fail(OSLALM_ERR_ARG, "problem %d is NULL", s);
         if (is_3d(p->g)) return fail(OSLALM_ERR_ARG, "batches hold 2D problems only (problem %d)", s);
         if (!p->initialized) return fail(OSLALM_ERR_STATE, "problem %d: call oslalm_init first", s);
+        if (p->p.n_inner != 1) return fail(OSLALM_ERR_ARG, "problem %d: batches run n_inner = 1", s);
         if (p->j_host % p->p.M) return fail(OSLALM_ERR_STATE, "problem %d is not at a whole iteration", s);
     }
     oslalm_batch *b = new (std::nothrow) oslalm_batch();

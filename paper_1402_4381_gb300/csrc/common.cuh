@@ -244,5 +244,14 @@ int launch_update3d(int nx, int ny, int nz, const float *x, float *xo, const flo
                     float inv_delta, int nbr, int curv_mode, cudaStream_t s);
 int launch_reg_value3d(int nx, int ny, int nz, const float *x, double beta, double delta, int nbr,
                        double *partials, int *nparts, cudaStream_t s);
+// inner FISTA step i >= 1: (v, x_k, u) -> u+, and v+ unless vo is null
+int launch_fista2d(int nx, int ny, const float *v, const float *xk, const float *u, float *uo, float *vo,
+                   const float *zeta, const float *g, const void *D, int d_dtype, const float *dscale,
+                   const DevState *st, float beta, float inv_delta, int nbr, int curv_mode, float gamma,
+                   cudaStream_t s);
+int launch_fista3d(int nx, int ny, int nz, const float *v, const float *xk, const float *u, float *uo, float *vo,
+                   const float *zeta, const float *g, const void *D, int d_dtype, const float *dscale,
+                   const DevState *st, float beta, float inv_delta, int nbr, int curv_mode, float gamma,
+                   cudaStream_t s);
 
 }  // namespace oslalm

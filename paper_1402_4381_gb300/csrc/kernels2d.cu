@@ -151,6 +151,20 @@ __global__ void __launch_bounds__(256) update2d_kernel(int nx, int ny, const flo
                                 (float)st->rho, beta, inv_delta, curv_mode);
 }
 
+template <typename DT, int NBR>
+__global__ void __launch_bounds__(256) fista2d_kernel(int nx, int ny, const float *__restrict__ v,
+                                                      const float *__restrict__ xk, const float *__restrict__ u,
+                                                      float *__restrict__ uo, float *__restrict__ vo,
+                                                      const float *__restrict__ zeta, const float *__restrict__ gs,
+                                                      const DT *__restrict__ D, const float *__restrict__ dscale,
+                                                      const DevState *__restrict__ st, float beta, float inv_delta,
+                                                      int curv_mode, float gamma) {
+    __shared__ float tile[10 * 34];
+    fista_tile<32, 8, DT, NBR>(tile, blockIdx.x * 32, blockIdx.y * 8, threadIdx.x, threadIdx.y,
+                               threadIdx.y * 32 + threadIdx.x, 256, nx, ny, v, xk, u, uo, vo, zeta, gs, D, dscale,
+                               (float)st->rho, beta, inv_delta, curv_mode, gamma);
+}
+
 template <int NBR>
 __global__ void __launch_bounds__(256) reg_value2d_kernel(int nx, int ny, const float *__restrict__ x, double beta,
                                                           double delta, double *__restrict__ partials) {
@@ -249,6 +263,28 @@ int launch_update2d(int nx, int ny, const float *x, float *xo, const float *zeta
     }
 #undef OSL_UPD
     OSL_LAUNCH_CHECK("update2d_kernel");
+    return OSLALM_OK;
+}
+
+int launch_fista2d(int nx, int ny, const float *v, const float *xk, const float *u, float *uo, float *vo,
+                   const float *zeta, const float *g, const void *D, int d_dtype, const float *dscale,
+                   const DevState *st, float beta, float inv_delta, int nbr, int curv_mode, float gamma,
+                   cudaStream_t s) {
+    dim3 block(32, 8), grid((nx + 31) / 32, (ny + 7) / 8);
+#define OSL_FIS(DT, N)                                                                                            \
+    fista2d_kernel<DT, N><<<grid, block, 0, s>>>(nx, ny, v, xk, u, uo, vo, zeta, g, (const DT *)D, dscale, st, beta, \
+                                                 inv_delta, curv_mode, gamma)
+    if (nbr == 8) {
+        if (d_dtype == OSLALM_F32) OSL_FIS(float, 8);
+        else if (d_dtype == OSLALM_F16) OSL_FIS(__half, 8);
+        else OSL_FIS(__nv_bfloat16, 8);
+    } else {
+        if (d_dtype == OSLALM_F32) OSL_FIS(float, 4);
+        else if (d_dtype == OSLALM_F16) OSL_FIS(__half, 4);
+        else OSL_FIS(__nv_bfloat16, 4);
+    }
+#undef OSL_FIS
+    OSL_LAUNCH_CHECK("fista2d_kernel");
     return OSLALM_OK;
 }
 

@@ -410,19 +410,15 @@ __device__ __forceinline__ void nbr3d(int k, int &ox, int &oy, int &oz) {
     oz = idx / 9 - 1;
 }
 
-template <typename DT, int NBR>
-__global__ void __launch_bounds__(256) update3d_kernel(int nx, int ny, int nz, const float *__restrict__ x,
-                                                       float *__restrict__ xo, const float *__restrict__ zeta,
-                                                       const float *__restrict__ gs, const DT *__restrict__ D,
-                                                       const float *__restrict__ dscale,
-                                                       const DevState *__restrict__ st, float beta,
-                                                       float inv_delta, int curv_mode) {
-    const int ix = blockIdx.x * 32 + threadIdx.x, iy = blockIdx.y * 8 + threadIdx.y, iz = blockIdx.z;
-    if (ix >= nx || iy >= ny) return;
+// Hyperbola-regularizer gradient and Huber (or maximum) curvature at voxel
+// (ix, iy, iz) of x over the 6- or 26-neighbourhood, before the beta and
+// 2 beta scaling.
+template <int NBR>
+__device__ __forceinline__ void stencil3d(const float *__restrict__ x, int nx, int ny, int nz, int ix, int iy, int iz,
+                                          float xj, float inv_delta, int curv_mode, float &grad, float &curv) {
     const size_t sxy = (size_t)nx * ny;
-    const size_t p = (size_t)iz * sxy + (size_t)iy * nx + ix;
-    const float xj = __ldg(x + p);
-    float grad = 0.f, curv = 0.f;
+    grad = 0.f;
+    curv = 0.f;
 #pragma unroll
     for (int k = 0; k < 26; ++k) {
         int ox, oy, oz;
@@ -438,6 +434,21 @@ __global__ void __launch_bounds__(256) update3d_kernel(int nx, int ny, int nz, c
         grad = fmaf(wk * t, q, grad);
         curv += wk * (curv_mode == OSLALM_CURV_HUBER ? q : 1.f);
     }
+}
+
+template <typename DT, int NBR>
+__global__ void __launch_bounds__(256) update3d_kernel(int nx, int ny, int nz, const float *__restrict__ x,
+                                                       float *__restrict__ xo, const float *__restrict__ zeta,
+                                                       const float *__restrict__ gs, const DT *__restrict__ D,
+                                                       const float *__restrict__ dscale,
+                                                       const DevState *__restrict__ st, float beta,
+                                                       float inv_delta, int curv_mode) {
+    const int ix = blockIdx.x * 32 + threadIdx.x, iy = blockIdx.y * 8 + threadIdx.y, iz = blockIdx.z;
+    if (ix >= nx || iy >= ny) return;
+    const size_t p = (size_t)iz * nx * ny + (size_t)iy * nx + ix;
+    const float xj = __ldg(x + p);
+    float grad, curv;
+    stencil3d<NBR>(x, nx, ny, nz, ix, iy, iz, xj, inv_delta, curv_mode, grad, curv);
     grad *= beta;
     curv *= 2.f * beta;
     const float rho = (float)st->rho;
@@ -445,6 +456,32 @@ __global__ void __launch_bounds__(256) update3d_kernel(int nx, int ny, int nz, c
     const float den = rho * (load_w(D, p) * __ldg(dscale)) + curv;
     const float xn = xj - (s + grad) / den;
     xo[p] = fmaxf(xn, 0.f);
+}
+
+// inner FISTA step i >= 1 (see fista_tile in proj2d.cuh), 3D stencil
+template <typename DT, int NBR>
+__global__ void __launch_bounds__(256) fista3d_kernel(int nx, int ny, int nz, const float *__restrict__ v,
+                                                      const float *__restrict__ xk, const float *__restrict__ u,
+                                                      float *__restrict__ uo, float *__restrict__ vo,
+                                                      const float *__restrict__ zeta, const float *__restrict__ gs,
+                                                      const DT *__restrict__ D, const float *__restrict__ dscale,
+                                                      const DevState *__restrict__ st, float beta, float inv_delta,
+                                                      int curv_mode, float gamma) {
+    const int ix = blockIdx.x * 32 + threadIdx.x, iy = blockIdx.y * 8 + threadIdx.y, iz = blockIdx.z;
+    if (ix >= nx || iy >= ny) return;
+    const size_t p = (size_t)iz * nx * ny + (size_t)iy * nx + ix;
+    const float vj = __ldg(v + p);
+    float grad, curv;
+    stencil3d<NBR>(v, nx, ny, nz, ix, iy, iz, vj, inv_delta, curv_mode, grad, curv);
+    grad *= beta;
+    curv *= 2.f * beta;
+    const float rho = (float)st->rho;
+    const float s = rho * __ldg(zeta + p) + (1.f - rho) * __ldg(gs + p);
+    const float rd = rho * (load_w(D, p) * __ldg(dscale));
+    const float gphi = fmaf(rd, vj - __ldg(xk + p), s + grad);
+    const float un = fmaxf(vj - gphi / (rd + curv), 0.f);
+    uo[p] = un;
+    if (vo) vo[p] = fmaf(gamma, un - __ldg(u + p), un);
 }
 
 template <int NBR>
@@ -551,6 +588,28 @@ int launch_update3d(int nx, int ny, int nz, const float *x, float *xo, const flo
     }
 #undef OSL_UPD3
     OSL_LAUNCH_CHECK("update3d_kernel");
+    return OSLALM_OK;
+}
+
+int launch_fista3d(int nx, int ny, int nz, const float *v, const float *xk, const float *u, float *uo, float *vo,
+                   const float *zeta, const float *g, const void *D, int d_dtype, const float *dscale,
+                   const DevState *st, float beta, float inv_delta, int nbr, int curv_mode, float gamma,
+                   cudaStream_t s) {
+    dim3 block(32, 8), grid((nx + 31) / 32, (ny + 7) / 8, nz);
+#define OSL_FIS3(DT, N)                                                                                         \
+    fista3d_kernel<DT, N><<<grid, block, 0, s>>>(nx, ny, nz, v, xk, u, uo, vo, zeta, g, (const DT *)D, dscale, st, \
+                                                 beta, inv_delta, curv_mode, gamma)
+    if (nbr == 26) {
+        if (d_dtype == OSLALM_F32) OSL_FIS3(float, 26);
+        else if (d_dtype == OSLALM_F16) OSL_FIS3(__half, 26);
+        else OSL_FIS3(__nv_bfloat16, 26);
+    } else {
+        if (d_dtype == OSLALM_F32) OSL_FIS3(float, 6);
+        else if (d_dtype == OSLALM_F16) OSL_FIS3(__half, 6);
+        else OSL_FIS3(__nv_bfloat16, 6);
+    }
+#undef OSL_FIS3
+    OSL_LAUNCH_CHECK("fista3d_kernel");
     return OSLALM_OK;
 }
 

@@ -229,14 +229,40 @@ int compute_denominator(oslalm_problem *p, cudaStream_t st) {
     return OSLALM_OK;
 }
 
+// The x-update: the constrained denoising problem of Sec. IV-A by n inner
+// FISTA steps from x_in.  Step 0 is the projected SQS step from x_in (the
+// whole update when n = 1); step i >= 1 starts from the extrapolated point
+// v_i with the previous u_i; the last step writes x_out.  Buffers: u in
+// d_fu[0], d_fu[1] alternately, v in d_fv[0], d_fv[1] (never read and
+// written by one launch).
 int update_step(oslalm_problem *p, const float *x_in, float *x_out, cudaStream_t st) {
     const oslalm_geom_desc &d = p->g->d;
-    if (is_3d(p->g))
-        return launch_update3d(d.nx, d.ny, d.nz, x_in, x_out, p->d_zeta, p->d_g, p->d_D, p->p.d_dtype, p->d_dscale,
-                               p->d_state, (float)p->p.beta, (float)(1.0 / p->p.delta), p->p.nbr, p->p.curvature,
-                               st);
-    return launch_update2d(d.nx, d.ny, x_in, x_out, p->d_zeta, p->d_g, p->d_D, p->p.d_dtype, p->d_dscale,
-                           p->d_state, (float)p->p.beta, (float)(1.0 / p->p.delta), p->p.nbr, p->p.curvature, st);
+    const int n = p->p.n_inner;
+    const float beta = (float)p->p.beta, inv_delta = (float)(1.0 / p->p.delta);
+    float *u0 = n == 1 ? x_out : p->d_fu[0];
+    int rc = is_3d(p->g)
+                 ? launch_update3d(d.nx, d.ny, d.nz, x_in, u0, p->d_zeta, p->d_g, p->d_D, p->p.d_dtype, p->d_dscale,
+                                   p->d_state, beta, inv_delta, p->p.nbr, p->p.curvature, st)
+                 : launch_update2d(d.nx, d.ny, x_in, u0, p->d_zeta, p->d_g, p->d_D, p->p.d_dtype, p->d_dscale,
+                                   p->d_state, beta, inv_delta, p->p.nbr, p->p.curvature, st);
+    if (rc || n == 1) return rc;
+    // after step 0: u_1 = v_1 (gamma_0 = 0), both in d_fu[0]
+    const float *v = p->d_fu[0], *u = p->d_fu[0];
+    for (int i = 1; i < n; ++i) {
+        const bool last = i == n - 1;
+        float *uo = last ? x_out : p->d_fu[i & 1];
+        float *vo = last ? nullptr : p->d_fv[(i - 1) & 1];
+        const float gm = p->fista_gamma[i];
+        rc = is_3d(p->g) ? launch_fista3d(d.nx, d.ny, d.nz, v, x_in, u, uo, vo, p->d_zeta, p->d_g, p->d_D,
+                                          p->p.d_dtype, p->d_dscale, p->d_state, beta, inv_delta, p->p.nbr,
+                                          p->p.curvature, gm, st)
+                         : launch_fista2d(d.nx, d.ny, v, x_in, u, uo, vo, p->d_zeta, p->d_g, p->d_D, p->p.d_dtype,
+                                          p->d_dscale, p->d_state, beta, inv_delta, p->p.nbr, p->p.curvature, gm, st);
+        if (rc) return rc;
+        v = vo;
+        u = uo;
+    }
+    return OSLALM_OK;
 }
 
 int bp_update(oslalm_problem *p, int next, cudaStream_t st) {
@@ -319,6 +345,7 @@ void free_problem(oslalm_problem *p) {
     cudaFree(p->d_dscale); cudaFree(p->d_maxbits); cudaFree(p->d_g); cudaFree(p->d_zeta); cudaFree(p->d_xalt);
     cudaFree(p->d_r); cudaFree(p->d_tmp); cudaFree(p->d_state); cudaFree(p->d_partials); cudaFree(p->d_stats);
     cudaFree(p->d_replay);
+    cudaFree(p->d_fu[0]); cudaFree(p->d_fu[1]); cudaFree(p->d_fv[0]); cudaFree(p->d_fv[1]);
     delete p;
 }
 
@@ -356,7 +383,7 @@ int oslalm_problem_create(const oslalm_geom *g, const float *y, const float *w, 
     if (!(pp.beta >= 0) || !(pp.delta > 0)) return fail(OSLALM_ERR_ARG, "need beta >= 0 and delta > 0");
     if (!is_3d(g) && pp.nbr != 4 && pp.nbr != 8) return fail(OSLALM_ERR_ARG, "2D neighbourhood must be 4 or 8");
     if (is_3d(g) && pp.nbr != 6 && pp.nbr != 26) return fail(OSLALM_ERR_ARG, "3D neighbourhood must be 6 or 26");
-    if (pp.n_inner != 1) return fail(OSLALM_ERR_RANGE, "only n_inner = 1 is implemented");
+    if (pp.n_inner < 1 || pp.n_inner > 64) return fail(OSLALM_ERR_RANGE, "need 1 <= n_inner <= 64");
     if (pp.rho_mode < 0 || pp.rho_mode > 2) return fail(OSLALM_ERR_ARG, "bad rho_mode");
     if (pp.rho_mode == OSLALM_RHO_FIXED && !(pp.rho_fixed > 0)) return fail(OSLALM_ERR_ARG, "rho_fixed must be > 0");
     if (pp.rho_mode != OSLALM_RHO_FIXED && !(pp.rho_min > 0 && pp.rho_min <= 1)) return fail(OSLALM_ERR_ARG, "need 0 < rho_min <= 1");
@@ -367,6 +394,14 @@ int oslalm_problem_create(const oslalm_geom *g, const float *y, const float *w, 
     if (!p) return fail(OSLALM_ERR_ALLOC, "host allocation failed");
     p->g = g;
     p->p = pp;
+    {  // FISTA momentum gamma_i = (tau_i - 1) / tau_{i+1}, tau_0 = 1 (Beck & Teboulle)
+        double tau = 1.0;
+        for (int i = 0; i < pp.n_inner; ++i) {
+            const double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * tau * tau));
+            p->fista_gamma.push_back((float)((tau - 1.0) / tn));
+            tau = tn;
+        }
+    }
     const oslalm_geom_desc &d = g->d;
     p->npix = (long)d.nx * d.ny * d.nz;
     p->per_view = d.nt * d.ns;
@@ -411,6 +446,12 @@ int oslalm_problem_create(const oslalm_geom *g, const float *y, const float *w, 
     OSL_ALLOC(p->d_r, sizeof(float) * nr);
     OSL_ALLOC(p->d_state, sizeof(DevState));
     OSL_ALLOC(p->d_partials, sizeof(double) * p->n_partials);
+    if (pp.n_inner > 1) {
+        for (int k = 0; k < 2; ++k) {
+            OSL_ALLOC(p->d_fu[k], sizeof(float) * p->npix);
+            OSL_ALLOC(p->d_fv[k], sizeof(float) * p->npix);
+        }
+    }
 #undef OSL_ALLOC
     if (e != cudaSuccess) {
         free_problem(p);

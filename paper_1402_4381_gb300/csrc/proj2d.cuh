@@ -194,17 +194,38 @@ __device__ __forceinline__ float bp_pixel_sum(const Geo2 &g, const float *__rest
     return acc;
 }
 
-// The n = 1 inner step on one TX x TY tile of pixels (Sec. IV-A):
-// s = rho zeta + (1-rho) g; x+ = max(0, x - (s + grad R(x)) / (rho D + D_R(x))),
-// with the 4/8-neighbour hyperbola gradient and Huber curvature read from a
-// shared-memory copy of the tile and its one-pixel halo.  (tx, ty): this
-// thread's pixel in the tile; tid/nthreads: its rank for the cooperative load.
-template <int TX, int TY, typename DT, int NBR>
-__device__ __forceinline__ void update_tile(float *tile, int ix0, int iy0, int tx, int ty, int tid, int nthreads,
-                                            int nx, int ny, const float *__restrict__ x, float *__restrict__ xo,
-                                            const float *__restrict__ zeta, const float *__restrict__ gs,
-                                            const DT *__restrict__ D, const float *__restrict__ dscale, float rho,
-                                            float beta, float inv_delta, int curv_mode) {
+// Hyperbola-regularizer gradient and Huber (or maximum) curvature at pixel
+// (tx, ty) of a shared-memory tile with a one-pixel halo (row width TX + 2):
+// grad = sum_k w_k psi'(x_j - x_k), curv = sum_k w_k omega(x_j - x_k), both
+// still to be scaled by beta and 2 beta.
+template <int TX, int NBR>
+__device__ __forceinline__ void stencil2d(const float *tile, int tx, int ty, int ix, int iy, int nx, int ny,
+                                          float inv_delta, int curv_mode, float &grad, float &curv) {
+    constexpr int W = TX + 2;
+    const float xj = tile[(ty + 1) * W + tx + 1];
+    grad = 0.f;
+    curv = 0.f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        int ox, oy;
+        nbr2d(k, ox, oy);
+        if (NBR == 4 && ox != 0 && oy != 0) continue;
+        const int nxp = ix + ox, nyp = iy + oy;
+        if (nxp < 0 || nxp >= nx || nyp < 0 || nyp >= ny) continue;
+        const float wk = (ox != 0 && oy != 0) ? 0.70710678118654752f : 1.f;
+        const float t = xj - tile[(ty + 1 + oy) * W + tx + 1 + ox];
+        const float u = t * inv_delta;
+        const float q = rsqrtf(fmaf(u, u, 1.f));
+        grad = fmaf(wk * t, q, grad);
+        curv += wk * (curv_mode == OSLALM_CURV_HUBER ? q : 1.f);
+    }
+}
+
+// Cooperative load of a TX x TY tile of x with its one-pixel halo (zeros
+// outside the image), then a barrier.
+template <int TX, int TY>
+__device__ __forceinline__ void load_tile_halo(float *tile, int ix0, int iy0, int tid, int nthreads, int nx, int ny,
+                                               const float *__restrict__ x) {
     constexpr int W = TX + 2, H = TY + 2;
     for (int k = tid; k < W * H; k += nthreads) {
         const int yy = k / W, xx = k - yy * W;
@@ -212,24 +233,26 @@ __device__ __forceinline__ void update_tile(float *tile, int ix0, int iy0, int t
         tile[k] = (gx >= 0 && gx < nx && gy >= 0 && gy < ny) ? __ldg(x + (size_t)gy * nx + gx) : 0.f;
     }
     __syncthreads();
+}
+
+// The n = 1 inner step on one TX x TY tile of pixels (Sec. IV-A):
+// s = rho zeta + (1-rho) g; x+ = max(0, x - (s + grad R(x)) / (rho D + D_R(x))),
+// with the 4/8-neighbour hyperbola gradient and Huber curvature read from a
+// shared-memory copy of the tile and its one-pixel halo.  (tx, ty): this
+// thread's pixel in the tile; tid/nthreads: its rank for the cooperative load.
+// This is also the first of n inner FISTA steps (from v = x).
+template <int TX, int TY, typename DT, int NBR>
+__device__ __forceinline__ void update_tile(float *tile, int ix0, int iy0, int tx, int ty, int tid, int nthreads,
+                                            int nx, int ny, const float *__restrict__ x, float *__restrict__ xo,
+                                            const float *__restrict__ zeta, const float *__restrict__ gs,
+                                            const DT *__restrict__ D, const float *__restrict__ dscale, float rho,
+                                            float beta, float inv_delta, int curv_mode) {
+    load_tile_halo<TX, TY>(tile, ix0, iy0, tid, nthreads, nx, ny, x);
     const int ix = ix0 + tx, iy = iy0 + ty;
     if (ix < nx && iy < ny) {
-        const float xj = tile[(ty + 1) * W + tx + 1];
-        float grad = 0.f, curv = 0.f;
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            int ox, oy;
-            nbr2d(k, ox, oy);
-            if (NBR == 4 && ox != 0 && oy != 0) continue;
-            const int nxp = ix + ox, nyp = iy + oy;
-            if (nxp < 0 || nxp >= nx || nyp < 0 || nyp >= ny) continue;
-            const float wk = (ox != 0 && oy != 0) ? 0.70710678118654752f : 1.f;
-            const float t = xj - tile[(ty + 1 + oy) * W + tx + 1 + ox];
-            const float u = t * inv_delta;
-            const float q = rsqrtf(fmaf(u, u, 1.f));
-            grad = fmaf(wk * t, q, grad);
-            curv += wk * (curv_mode == OSLALM_CURV_HUBER ? q : 1.f);
-        }
+        const float xj = tile[(ty + 1) * (TX + 2) + tx + 1];
+        float grad, curv;
+        stencil2d<TX, NBR>(tile, tx, ty, ix, iy, nx, ny, inv_delta, curv_mode, grad, curv);
         grad *= beta;
         curv *= 2.f * beta;
         const size_t p = (size_t)iy * nx + ix;
@@ -237,6 +260,36 @@ __device__ __forceinline__ void update_tile(float *tile, int ix0, int iy0, int t
         const float den = rho * (load_w(D, p) * __ldg(dscale)) + curv;
         const float xn = xj - (s + grad) / den;
         xo[p] = fmaxf(xn, 0.f);
+    }
+}
+
+// Inner FISTA step i >= 1 of the constrained denoising problem
+//   min_{v >= 0} Phi(v) = R(v) + (rho/2) ||v - x_k + D^-1 s / rho||_D^2
+// from the extrapolated point v (tile): u+ = max(0, v - grad Phi(v) / (rho D
+// + D_R(v))), grad Phi(v) = grad R(v) + s + rho D (v - x_k); writes u+ and,
+// unless vo is null, the next extrapolated point u+ + gamma (u+ - u).
+template <int TX, int TY, typename DT, int NBR>
+__device__ __forceinline__ void fista_tile(float *tile, int ix0, int iy0, int tx, int ty, int tid, int nthreads,
+                                           int nx, int ny, const float *__restrict__ v, const float *__restrict__ xk,
+                                           const float *__restrict__ u, float *__restrict__ uo, float *__restrict__ vo,
+                                           const float *__restrict__ zeta, const float *__restrict__ gs,
+                                           const DT *__restrict__ D, const float *__restrict__ dscale, float rho,
+                                           float beta, float inv_delta, int curv_mode, float gamma) {
+    load_tile_halo<TX, TY>(tile, ix0, iy0, tid, nthreads, nx, ny, v);
+    const int ix = ix0 + tx, iy = iy0 + ty;
+    if (ix < nx && iy < ny) {
+        const float vj = tile[(ty + 1) * (TX + 2) + tx + 1];
+        float grad, curv;
+        stencil2d<TX, NBR>(tile, tx, ty, ix, iy, nx, ny, inv_delta, curv_mode, grad, curv);
+        grad *= beta;
+        curv *= 2.f * beta;
+        const size_t p = (size_t)iy * nx + ix;
+        const float s = rho * __ldg(zeta + p) + (1.f - rho) * __ldg(gs + p);
+        const float rd = rho * (load_w(D, p) * __ldg(dscale));
+        const float gphi = fmaf(rd, vj - __ldg(xk + p), s + grad);
+        const float un = fmaxf(vj - gphi / (rd + curv), 0.f);
+        uo[p] = un;
+        if (vo) vo[p] = fmaf(gamma, un - __ldg(u + p), un);
     }
 }
 
