@@ -334,7 +334,7 @@ def run_ours(args):
         traffic = bytes_px * g.nx * g.ny * g.nz
         achieved = traffic / (per[dom] / 1000.0)
         hbm = (pk or {}).get("hbm_gbs", 6800.0) * 1e9
-        roof = {"kernel": f"update{dim}_kernel", "bound": "hbm", "achieved": achieved / 1e9, "peak": hbm / 1e9,
+        roof = {"kernel": "update3d_kernel" if g.kind == 2 else "update2d_kernel", "bound": "hbm", "achieved": achieved / 1e9, "peak": hbm / 1e9,
                 "unit": "GB/s", "frac": achieved / hbm, "traffic": None}
     roof["per_kernel_ms"] = {k: round(v, 5) for k, v in per.items()}
 

@@ -54,9 +54,13 @@ __host__ __device__ __forceinline__ int ray_axis(int packed) { return packed & 1
 __host__ __device__ __forceinline__ int ray_n0(int packed) { return (int)((unsigned)packed << 16) >> 17; }
 __host__ __device__ __forceinline__ int ray_k(int packed) { return packed >> 16; }
 
-// Per-view parameters: beam direction u = (cu, su).
+// Per-view parameters: beam direction u = (cu, su).  In a 2D view the rays
+// of channels [0, split) advance along axis axis0 (0: x, 1: y) and those of
+// [split, ns) along the other (a fan narrower than 90 degrees switches at
+// most once).
 struct __align__(16) View2 {
-    float cu, su, pad0, pad1;
+    float cu, su;
+    int split, axis0;
 };
 
 // 3D cone-beam per-view parameters (FP32 copies of FP64 set-up values).
@@ -82,7 +86,13 @@ struct __align__(16) Ray3 {
     float z0h, z0l, w1l, q;
     int kw, sw, oz_i;
     float oz_f, oz_fl;  // oz - oz_i as a float pair
-    float pad0, pad1, pad2;
+    // FP32 rounding residues of xy.f0 and xy.kappa_lo.  A ray within a few
+    // hundredths of a degree of an axis (slope kappa ~ 1e-3) splits a row
+    // between two voxels at a fraction whose error is the position error
+    // divided by kappa, so the transaxial span carries these in its
+    // compensated sum.
+    float f0l, kll;
+    float pad2;
 };
 struct Geo3 {  // kernel-side cone geometry (by value)
     int nx, ny, nz, ns, nt, nviews;

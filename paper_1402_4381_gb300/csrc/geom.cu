@@ -44,8 +44,11 @@ static double view_turns(const oslalm_geom_desc &d, int v) {
     return d.angle_start / M_PI + (double)v * (d.angle_span / M_PI) / (double)d.nviews;
 }
 
-// Parameters of the 2D line through P with unit direction (dx_, dy_).
-static Ray2 make_ray2(const oslalm_geom_desc &d, double px, double py, double ux, double uy) {
+// Parameters of the 2D line through P with unit direction (dx_, dy_).  If
+// lo is given, it receives the FP32 rounding residues of f0 and kappa_lo
+// (exact value minus the stored float), for callers that carry them.
+static Ray2 make_ray2(const oslalm_geom_desc &d, double px, double py, double ux, double uy,
+                      float *lo = nullptr) {
     const double xlo = d.offset_x - 0.5 * d.nx * d.dx;
     const double ylo = d.offset_y - 0.5 * d.ny * d.dy;
     const double ax = ux / d.dx, ay = uy / d.dy;  // direction in index units
@@ -78,6 +81,10 @@ static Ray2 make_ray2(const oslalm_geom_desc &d, double px, double py, double ux
     r.kappa_lo = (float)(kappa - k / 2048.0);
     r.lrow = misses ? 0.f : (float)lrow;
     r.packed = (int)((unsigned)k << 16) | (((int)n0 & 0x7fff) << 1) | axis;
+    if (lo) {
+        lo[0] = misses ? 0.f : (float)((b0 - n0) - (double)r.f0);
+        lo[1] = (float)((kappa - k / 2048.0) - (double)r.kappa_lo);
+    }
     return r;
 }
 
@@ -133,7 +140,10 @@ static void ray3_table_view(const oslalm_geom_desc &d, int v, Ray3 *out) {
         double ld = sqrt(dxv * dxv + dyv * dyv);
         double ux = dxv / ld, uy = dyv / ld;
         Ray3 r;
-        r.xy = make_ray2(d, sx, sy, ux, uy);
+        float lo[2];
+        r.xy = make_ray2(d, sx, sy, ux, uy, lo);
+        r.f0l = lo[0];
+        r.kll = lo[1];
         int axis = ray_axis(r.xy.packed);
         double u_a = axis ? uy : ux;
         double s_a = axis ? sy : sx;
@@ -167,7 +177,7 @@ static void ray3_table_view(const oslalm_geom_desc &d, int v, Ray3 *out) {
         r.oz_i = (int)ozi;
         r.oz_f = (float)(oz - ozi);
         r.oz_fl = (float)((oz - ozi) - (double)r.oz_f);
-        r.pad0 = r.pad1 = r.pad2 = 0.f;
+        r.pad2 = 0.f;
         r.q = (float)(d.dt / (2.0 * ld));
         out[c] = r;
     }
@@ -290,12 +300,24 @@ int oslalm_geom_create(const oslalm_geom_desc *desc, oslalm_geom **out) {
     for (int v = 0; v < d.nviews; ++v) {
         double cu, su;
         cos_sin_turns(view_turns(d, v), &cu, &su);
-        views[v] = View2{(float)cu, (float)su, 0.f, 0.f};
+        views[v] = View2{(float)cu, (float)su, d.ns, 0};
         views3[v] = View3{(float)cu, (float)su, (float)(-d.dso * cu), (float)(-d.dso * su)};
         allv[v] = v;
         if (two_d) {
             ray_table_view(d, v, rview.data());
             for (int c = 0; c < d.ns; ++c) rays[(size_t)v * d.ns + c] = make_rayp(rview[c]);
+            // channels [0, split) share the orientation axis0, [split, ns) the other
+            const int a0 = ray_axis(rview[0].packed);
+            int split = 0;
+            while (split < d.ns && ray_axis(rview[split].packed) == a0) ++split;
+            for (int c = split; c < d.ns; ++c)
+                if (ray_axis(rview[c].packed) == a0) {
+                    delete g;
+                    return fail(OSLALM_ERR_RANGE,
+                                "view %d: rays switch orientation more than once (fan angle of 90 degrees or more)", v);
+                }
+            views[v].split = split;
+            views[v].axis0 = a0;
         }
         else ray3_table_view(d, v, &rays3[(size_t)v * d.ns]);
     }

@@ -4,8 +4,11 @@
 //           ray/pixel lengths), one thread per ray marching along its major
 //           axis; epilogue writes either A_m x or the weighted residual
 //           M W_m (A_m x - y_m) of Eq. os_lalm_iterates.
-//  bp2d   : pixel-driven gather back-projection A_m' r with the same
-//           per-(ray,pixel) weights (exact transpose, no atomics); epilogues
+//  bp2d   : gather back-projection A_m' r over pixel tiles with the same
+//           per-(ray,pixel) weights (exact transpose, no atomics): each
+//           thread owns a strip of pixels along a major row of the rays, so
+//           one evaluation of a ray's row weights serves both pixels it
+//           touches; epilogues
 //           store / accumulate, initialise zeta = g, or apply the split-
 //           gradient update g+ = (rho zeta+ + g)/(rho+1), the restart
 //           indicator xi = (g - zeta+)'(zeta+ - zeta) (Eq. period_indicator_qp,
@@ -82,9 +85,8 @@ __global__ void __launch_bounds__(128) cost2d_kernel(Geo2 g, const float *__rest
 }
 
 // ---------------------------------------------------------------- back-projection
-// Block of 8 warps over a 32 x 4 pixel tile: warp w takes view group w % 4
-// for pixel rows w / 4 and w / 4 + 2 (two independent chains per thread);
-// the group partials meet in shared memory and are added in group order.
+// One block of kBpThreads threads per kBpTile^2 pixel tile (bp_tile_strips);
+// then each thread finishes two pixels of the tile.
 template <int MODE>
 __device__ __forceinline__ double bp2d_epilogue(const UpdateArgs &ua, float *out, size_t p, float acc) {
     if (MODE == BP_STORE) {
@@ -109,30 +111,21 @@ __device__ __forceinline__ double bp2d_epilogue(const UpdateArgs &ua, float *out
 }
 
 template <int MODE>
-__global__ void __launch_bounds__(256) bp2d_kernel(Geo2 g, const float *__restrict__ r, float *__restrict__ out,
-                                                   const int *__restrict__ views, int nv, UpdateArgs ua) {
-    __shared__ float part[kBpGroups][4][32];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int grp = warp & 3, row = warp >> 2;
-    const int ix = blockIdx.x * 32 + lane;
-    const int iy0 = blockIdx.y * 4 + row, iy1 = iy0 + 2;
-    float a = 0.f, b = 0.f;
-    if (ix < g.nx && iy0 < g.ny)
-        bp_pixel_range2(g, r, views, bp_group_begin(nv, grp), bp_group_begin(nv, grp + 1), ix, iy0, iy1, iy1 < g.ny,
-                        a, b);
-    part[grp][row][lane] = a;
-    part[grp][row + 2][lane] = b;
+__global__ void __launch_bounds__(kBpThreads) bp2d_kernel(Geo2 g, const float *__restrict__ r,
+                                                          float *__restrict__ out, const int *__restrict__ views,
+                                                          int nv, UpdateArgs ua) {
+    __shared__ BpTileAcc S;
+    const int tx0 = blockIdx.x * kBpTile, ty0 = blockIdx.y * kBpTile;
+    bp_tile_strips(g, r, views, nv, tx0, ty0, threadIdx.x, S);
     __syncthreads();
     double xi_local = 0.0;
-    if (threadIdx.x < 128) {
-        const int pr = threadIdx.x >> 5;
-        const int px = blockIdx.x * 32 + lane, py = blockIdx.y * 4 + pr;
-        if (px < g.nx && py < g.ny) {
-            float acc = 0.f;
 #pragma unroll
-            for (int k = 0; k < kBpGroups; ++k) acc += part[k][pr][lane];
-            xi_local = bp2d_epilogue<MODE>(ua, out, (size_t)py * g.nx + px, acc);
-        }
+    for (int k = 0; k < kBpTile * kBpTile / kBpThreads; ++k) {
+        const int i = threadIdx.x + k * kBpThreads;
+        const int px = i % kBpTile, py = i / kBpTile;
+        const int ix = tx0 + px, iy = ty0 + py;
+        if (ix < g.nx && iy < g.ny)
+            xi_local += bp2d_epilogue<MODE>(ua, out, (size_t)iy * g.nx + ix, bp_tile_total(S, px, py));
     }
     if (MODE == BP_UPDATE) subset_iteration_epilogue(ua, xi_local);
 }
@@ -189,7 +182,7 @@ __global__ void __launch_bounds__(256) reg_value2d_kernel(int nx, int ny, const 
 }
 
 // ---------------------------------------------------------------- launchers
-int bp2d_blocks(const Geo2 &g) { return ((g.nx + 31) / 32) * ((g.ny + 3) / 4); }
+int bp2d_blocks(const Geo2 &g) { return ((g.nx + kBpTile - 1) / kBpTile) * ((g.ny + kBpTile - 1) / kBpTile); }
 
 template <int MODE>
 static int launch_fp2d_t(const Geo2 &g, const float *x, float *out, const int *views, int nv, const float *y,
@@ -216,7 +209,7 @@ int launch_fp2d(const Geo2 &g, const float *x, float *out, const int *views, int
 
 int launch_bp2d(const Geo2 &g, const float *r, float *out, const int *views, int nv, int mode, const UpdateArgs *ua,
                 cudaStream_t st) {
-    dim3 block(256), grid((g.nx + 31) / 32, (g.ny + 3) / 4);
+    dim3 block(kBpThreads), grid((g.nx + kBpTile - 1) / kBpTile, (g.ny + kBpTile - 1) / kBpTile);
     UpdateArgs a{};
     if (ua) a = *ua;
     switch (mode) {

@@ -123,7 +123,8 @@ __device__ __forceinline__ void dcell_frac(const DSpan &s, bool inc, float kk, f
 }
 
 // transaxial span of row ia, compensated like the height span: the centre
-// b(ia + 1/2) = n0 + (2 ia + 1) k / 4096 + f0 + (ia + 1/2) kappa_lo
+// b(ia + 1/2) = n0 + (2 ia + 1) k / 4096 + f0 + (ia + 1/2) kappa_lo, with the
+// float residues of f0 and kappa_lo added to the low part
 __device__ __forceinline__ DSpan bspan(const Ray3 &r, int ia) {
     const int k = ray_k(r.xy.packed);
     const int p = (2 * ia + 1) * k;  // exact: |p| < 2^24
@@ -134,7 +135,7 @@ __device__ __forceinline__ DSpan bspan(const Ray3 &r, int ia) {
     float s, e, s2, e2;
     two_sum(r.xy.f0, fr, s, e);
     two_sum(s, pr, s2, e2);
-    const float lo_part = __fadd_rn(__fadd_rn(e, e2), pe);
+    const float lo_part = __fadd_rn(__fadd_rn(__fadd_rn(e, e2), pe), __fmaf_rn(ac, r.kll, r.f0l));
     DSpan o;
     o.base = ray_n0(r.xy.packed) + (p >> 12);
     o.ch = __fmul_rn(rintf(__fmul_rn(s2, 1048576.f)), 9.5367431640625e-7f);

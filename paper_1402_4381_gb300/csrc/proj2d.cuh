@@ -125,48 +125,21 @@ __device__ __forceinline__ float chord_px(const RayP &r, const PixF &p) {
     return d == 0.f ? w.w0 : (d == 1.f ? w.w1 : 0.f);
 }
 
-// The back-projected value of a pixel is summed in kBpGroups consecutive
-// view groups [begin(k), begin(k+1)): each group's partial in view order
-// (channels ascending within a view), then the partials in group order.  The
-// single-problem kernel gives the groups to different warps; the batched
-// kernel sums them in one thread; both give the same bits.
+// The back-projected value of a pixel is summed in a fixed order: the views
+// are cut into kBpGroups consecutive groups [begin(k), begin(k+1)); within a
+// group the contributions of the x-major rays (views ascending, channels
+// ascending) and of the y-major rays (same order) are summed separately, by
+// fused multiply-adds, and added; the group totals are added in group order.
+// The tiled kernel and the pixel-by-pixel function below follow this order,
+// so they give the same bits.
 constexpr int kBpGroups = 4;
 __device__ __forceinline__ int bp_group_begin(int nv, int k) { return (nv * k) / kBpGroups; }
 
-// Sum over views [lv0, lv1) of length x r for pixels (ix, iy0) and (ix, iy1)
-// (two independent chains; has1 = false: only the first pixel).
-__device__ __forceinline__ void bp_pixel_range2(const Geo2 &g, const float *__restrict__ r,
-                                                const int *__restrict__ views, int lv0, int lv1, int ix, int iy0,
-                                                int iy1, bool has1, float &acc0, float &acc1) {
-    acc0 = 0.f;
-    acc1 = 0.f;
-    const float px = g.xlo + ((float)ix + 0.5f) * g.dx;
-    const float py0 = g.ylo + ((float)iy0 + 0.5f) * g.dy;
-    const float py1 = g.ylo + ((float)iy1 + 0.5f) * g.dy;
-    const PixF pf0 = pix_f(ix, iy0), pf1 = pix_f(ix, iy1);
-    for (int lv = lv0; lv < lv1; ++lv) {
-        const int v = __ldg(views + lv);
-        if ((unsigned)v >= (unsigned)g.nviews) continue;  // caller-supplied view out of range
-        const View2 vw = g.views[v];
-        int a0, a1, b0, b1;
-        channel_window(g, vw, px, py0, a0, a1);
-        channel_window(g, vw, px, py1, b0, b1);
-        if (!has1) b1 = b0 - 1;
-        const RayP *rr = g.rays + (size_t)v * g.ns;
-        const float *rv = r + (size_t)lv * g.ns;
-        const int n = max(a1 - a0, b1 - b0) + 1;
-        for (int k = 0; k < n; ++k) {
-            const int ca = a0 + k, cb = b0 + k;
-            if (ca <= a1) acc0 = fmaf(chord_px(rr[ca], pf0), __ldg(rv + ca), acc0);
-            if (cb <= b1) acc1 = fmaf(chord_px(rr[cb], pf1), __ldg(rv + cb), acc1);
-        }
-    }
-}
-
-// Sum over views [lv0, lv1) of length x r for the rays crossing pixel (ix, iy).
+// Sum over views [lv0, lv1) of length x r for the rays crossing pixel (ix, iy),
+// in the order above.
 __device__ __forceinline__ float bp_pixel_range(const Geo2 &g, const float *__restrict__ r,
                                                 const int *__restrict__ views, int lv0, int lv1, int ix, int iy) {
-    float acc = 0.f;
+    float accx = 0.f, accy = 0.f;
     const float px = g.xlo + ((float)ix + 0.5f) * g.dx;
     const float py = g.ylo + ((float)iy + 0.5f) * g.dy;
     const PixF pf = pix_f(ix, iy);
@@ -178,19 +151,146 @@ __device__ __forceinline__ float bp_pixel_range(const Geo2 &g, const float *__re
         channel_window(g, vw, px, py, c0, c1);
         const RayP *rr = g.rays + (size_t)v * g.ns;
         const float *rv = r + (size_t)lv * g.ns;
-#pragma unroll 2
-        for (int c = c0; c <= c1; ++c) acc = fmaf(chord_px(rr[c], pf), __ldg(rv + c), acc);
+        for (int c = c0; c <= c1; ++c) {
+            const RayP rp = rr[c];
+            const float t = chord_px(rp, pf);
+            const float val = __ldg(rv + c);
+            if (rp.axis) accy = fmaf(t, val, accy);
+            else accx = fmaf(t, val, accx);
+        }
     }
-    return acc;
+    return accx + accy;
 }
 
-// A'r at pixel (ix, iy) over the listed views, in the grouped order above.
+// A'r at pixel (ix, iy) over the listed views, in the order above.
 __device__ __forceinline__ float bp_pixel_sum(const Geo2 &g, const float *__restrict__ r,
                                               const int *__restrict__ views, int nv, int ix, int iy) {
     float acc = 0.f;
 #pragma unroll
     for (int k = 0; k < kBpGroups; ++k)
         acc += bp_pixel_range(g, r, views, bp_group_begin(nv, k), bp_group_begin(nv, k + 1), ix, iy);
+    return acc;
+}
+
+// ---------------------------------------------------------------- tiled back-projection
+// A tile of kBpTile x kBpTile pixels is back-projected by 32 x kBpGroups
+// threads: warp k takes view group k.  For the x-major rays a lane owns the
+// vertical strip (one column, kBpStrip rows); for the y-major rays the
+// horizontal strip (one row, kBpStrip columns).  Every pixel of a strip lies
+// in the same major row of those rays, so one evaluation of a ray's row
+// weights (first pixel j, lengths w0 and w1) serves both pixels it touches;
+// the strip's candidate rays are the channel window of the whole strip.
+constexpr int kBpTile = 16;
+constexpr int kBpStrip = 8;
+constexpr int kBpPitch = kBpTile + 1;  // padded row of the shared accumulators
+constexpr int kBpThreads = 32 * kBpGroups;
+
+struct BpTileAcc {  // [view group][0: x-major, 1: y-major][row * kBpPitch + column]
+    float a[kBpGroups][2][kBpTile * kBpPitch];
+};
+
+// Channel window of a strip of pixels whose centres run from (pxa, pya) to
+// (pxb, pyb), half_len apart from its middle: channels whose ray may cross
+// any pixel of it.  The channel coordinate of a point is linear (parallel
+// beam) or monotone (fan: the angle seen from the source) along a segment,
+// so the end pixels span the centres; the half-width takes the smallest
+// distance from the source that any point of the segment can have.  Margins
+// as in channel_window.
+__device__ __forceinline__ void strip_window(const Geo2 &g, const View2 &vw, float pxa, float pya, float pxb,
+                                             float pyb, float half_len, int &c0, int &c1) {
+    float ca, cb, hw;
+    if (g.kind == OSLALM_PAR2D) {
+        constexpr float kMargin = 0.02f;
+        ca = (-pxa * vw.su + pya * vw.cu) * g.inv_ds + g.c0;
+        cb = (-pxb * vw.su + pyb * vw.cu) * g.inv_ds + g.c0;
+        hw = 0.5f * (g.dx * fabsf(vw.su) + g.dy * fabsf(vw.cu)) * g.inv_ds + kMargin;
+    } else {
+        const float aa = pxa * vw.cu + pya * vw.su + g.dso, ba = -pxa * vw.su + pya * vw.cu;
+        const float ab = pxb * vw.cu + pyb * vw.su + g.dso, bb = -pxb * vw.su + pyb * vw.cu;
+        const float ga = g.fast_atan ? atan_unit(__fdividef(ba, aa)) : atan2f(ba, aa);
+        const float gb = g.fast_atan ? atan_unit(__fdividef(bb, ab)) : atan2f(bb, ab);
+        const float kMargin = 0.02f + 2.5e-6f * g.dsd * g.inv_ds;
+        const float dmin = fmaxf(sqrtf(fminf(fmaf(aa, aa, ba * ba), fmaf(ab, ab, bb * bb))) - half_len, 0.f);
+        const float d2 = dmin * dmin - g.half_diag * g.half_diag;
+        const float ang = g.half_diag * rsqrtf(fmaxf(d2, 1e-12f));  // >= angular radius of any strip pixel
+        const float k = g.dsd * g.inv_ds;
+        ca = ga * k + g.c0;
+        cb = gb * k + g.c0;
+        hw = ang * 1.0001f * k + kMargin;
+    }
+    c0 = max(0, (int)ceilf(fminf(ca, cb) - hw));
+    c1 = min(g.ns - 1, (int)floorf(fmaxf(ca, cb) + hw));
+}
+
+// Back-projection of the tile with lower corner (tx0, ty0) over views
+// [0, nv) into S (thread t in [0, kBpThreads)); the caller synchronises the
+// block before reading S with bp_tile_total.
+__device__ __forceinline__ void bp_tile_strips(const Geo2 &g, const float *__restrict__ r,
+                                               const int *__restrict__ views, int nv, int tx0, int ty0, int t,
+                                               BpTileAcc &S) {
+    const int grp = t >> 5, lane = t & 31;
+    const int u = lane & (kBpTile - 1), s0 = (lane / kBpTile) * kBpStrip;
+    const int lv0 = bp_group_begin(nv, grp), lv1 = bp_group_begin(nv, grp + 1);
+#pragma unroll 1
+    for (int ax = 0; ax < 2; ++ax) {
+        float *A = S.a[grp][ax];
+        // accumulator of strip pixel d: x-major rays (vertical strip): row s0 + d
+        // of column u; y-major rays (horizontal strip): column s0 + d of row u
+        const int base = ax ? u * kBpPitch + s0 : s0 * kBpPitch + u;
+        const int step = ax ? 1 : kBpPitch;
+#pragma unroll
+        for (int d = 0; d < kBpStrip; ++d) A[base + d * step] = 0.f;
+        const int ia = (ax ? ty0 : tx0) + u;   // major row of the rays
+        const int jb0 = (ax ? tx0 : ty0) + s0;  // first minor index of the strip
+        const int Na = ax ? g.ny : g.nx, Nb = ax ? g.nx : g.ny;
+        if (ia >= Na || jb0 >= Nb) continue;
+        const int jb1 = min(jb0 + kBpStrip, Nb) - 1;
+        const float pa = ax ? g.dy : g.dx, pb = ax ? g.dx : g.dy;
+        const float am = (ax ? g.ylo : g.xlo) + ((float)ia + 0.5f) * pa;  // major coordinate (mm)
+        const float blo = (ax ? g.xlo : g.ylo) + ((float)jb0 + 0.5f) * pb;
+        const float bhi = (ax ? g.xlo : g.ylo) + ((float)jb1 + 0.5f) * pb;
+        const float pxa = ax ? blo : am, pya = ax ? am : blo;
+        const float pxb = ax ? bhi : am, pyb = ax ? am : bhi;
+        const float half_len = 0.5f * (float)(jb1 - jb0) * pb;
+        const float ia2 = (float)(2 * ia + 1), iah = (float)ia + 0.5f;
+        const float jbf = (float)jb0;
+        for (int lv = lv0; lv < lv1; ++lv) {
+            const int v = __ldg(views + lv);
+            if ((unsigned)v >= (unsigned)g.nviews) continue;  // caller-supplied view out of range
+            const View2 vw = g.views[v];
+            int k0 = 0, k1 = g.ns;  // channels of this view whose rays have this orientation
+            if (vw.axis0 == ax) k1 = vw.split;
+            else k0 = vw.split;
+            if (k0 >= k1) continue;
+            int c0, c1;
+            strip_window(g, vw, pxa, pya, pxb, pyb, half_len, c0, c1);
+            c0 = max(c0, k0);
+            c1 = min(c1, k1 - 1);
+            const RayP *rr = g.rays + (size_t)v * g.ns;
+            const float *rv = r + (size_t)lv * g.ns;
+            for (int c = c0; c <= c1; ++c) {
+                const RowW w = row_weights(rr[c], ia2, iah);
+                const float val = __ldg(rv + c);
+                const int d = (int)__fsub_rn(w.j, jbf);  // exact: both are small integers
+                if ((unsigned)d < (unsigned)kBpStrip) {
+                    float &p = A[base + d * step];
+                    p = fmaf(w.w0, val, p);
+                }
+                if ((unsigned)(d + 1) < (unsigned)kBpStrip) {
+                    float &p = A[base + (d + 1) * step];
+                    p = fmaf(w.w1, val, p);
+                }
+            }
+        }
+    }
+}
+
+// A'r at tile pixel (px, py) from the accumulators, in the fixed order.
+__device__ __forceinline__ float bp_tile_total(const BpTileAcc &S, int px, int py) {
+    const int i = py * kBpPitch + px;
+    float acc = 0.f;
+#pragma unroll
+    for (int k = 0; k < kBpGroups; ++k) acc += S.a[k][0][i] + S.a[k][1][i];
     return acc;
 }
 
