@@ -111,7 +111,7 @@ __device__ __forceinline__ double bp2d_epilogue(const UpdateArgs &ua, float *out
 }
 
 template <int MODE>
-__global__ void __launch_bounds__(kBpThreads) bp2d_kernel(Geo2 g, const float *__restrict__ r,
+__global__ void __launch_bounds__(kBpThreads, 8) bp2d_kernel(Geo2 g, const float *__restrict__ r,
                                                           float *__restrict__ out, const int *__restrict__ views,
                                                           int nv, UpdateArgs ua) {
     __shared__ BpTileAcc S;

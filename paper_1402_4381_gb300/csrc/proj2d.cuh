@@ -126,24 +126,23 @@ __device__ __forceinline__ float chord_px(const RayP &r, const PixF &p) {
 }
 
 // The back-projected value of a pixel is summed in a fixed order: the views
-// are cut into kBpGroups consecutive groups [begin(k), begin(k+1)); within a
-// group the contributions of the x-major rays (views ascending, channels
-// ascending) and of the y-major rays (same order) are summed separately, by
-// fused multiply-adds, and added; the group totals are added in group order.
-// The tiled kernel and the pixel-by-pixel function below follow this order,
-// so they give the same bits.
-constexpr int kBpGroups = 4;
-__device__ __forceinline__ int bp_group_begin(int nv, int k) { return (nv * k) / kBpGroups; }
+// are dealt to kBpGroups groups (list position lv goes to group lv mod
+// kBpGroups); within a group the contributions of the x-major rays (views in
+// list order, channels ascending) and of the y-major rays (same order) are
+// summed separately, by fused multiply-adds, and added; the group totals are
+// added in group order.  The tiled kernel and the pixel-by-pixel function
+// below follow this order, so they give the same bits.
+constexpr int kBpGroups = 8;
 
-// Sum over views [lv0, lv1) of length x r for the rays crossing pixel (ix, iy),
-// in the order above.
-__device__ __forceinline__ float bp_pixel_range(const Geo2 &g, const float *__restrict__ r,
-                                                const int *__restrict__ views, int lv0, int lv1, int ix, int iy) {
+// Sum over the views of group k of length x r for the rays crossing pixel
+// (ix, iy), in the order above.
+__device__ __forceinline__ float bp_pixel_group(const Geo2 &g, const float *__restrict__ r,
+                                                const int *__restrict__ views, int nv, int k, int ix, int iy) {
     float accx = 0.f, accy = 0.f;
     const float px = g.xlo + ((float)ix + 0.5f) * g.dx;
     const float py = g.ylo + ((float)iy + 0.5f) * g.dy;
     const PixF pf = pix_f(ix, iy);
-    for (int lv = lv0; lv < lv1; ++lv) {
+    for (int lv = k; lv < nv; lv += kBpGroups) {
         const int v = __ldg(views + lv);
         if ((unsigned)v >= (unsigned)g.nviews) continue;  // caller-supplied view out of range
         const View2 vw = g.views[v];
@@ -167,26 +166,28 @@ __device__ __forceinline__ float bp_pixel_sum(const Geo2 &g, const float *__rest
                                               const int *__restrict__ views, int nv, int ix, int iy) {
     float acc = 0.f;
 #pragma unroll
-    for (int k = 0; k < kBpGroups; ++k)
-        acc += bp_pixel_range(g, r, views, bp_group_begin(nv, k), bp_group_begin(nv, k + 1), ix, iy);
+    for (int k = 0; k < kBpGroups; ++k) acc += bp_pixel_group(g, r, views, nv, k, ix, iy);
     return acc;
 }
 
 // ---------------------------------------------------------------- tiled back-projection
 // A tile of kBpTile x kBpTile pixels is back-projected by 32 x kBpGroups
-// threads: warp k takes view group k.  For the x-major rays a lane owns the
-// vertical strip (one column, kBpStrip rows); for the y-major rays the
-// horizontal strip (one row, kBpStrip columns).  Every pixel of a strip lies
-// in the same major row of those rays, so one evaluation of a ray's row
-// weights (first pixel j, lengths w0 and w1) serves both pixels it touches;
-// the strip's candidate rays are the channel window of the whole strip.
+// threads: warp k takes view group k.  For the x-major rays lane l owns the
+// vertical strip of column (l mod 16), rows 8 (l / 16) + [0, 8); for the
+// y-major rays the horizontal strip of row (l mod 16), columns
+// 8 (l / 16) + [0, 8).  Every pixel of a strip lies in the same major row of
+// those rays, so one evaluation of a ray's row weights (first pixel j,
+// lengths w0 and w1) serves both pixels it touches; the strip's candidate
+// rays are the channel window of the whole strip.  Strip pixel d of lane l
+// accumulates in word d * 32 + l of its group's (and orientation's) block,
+// always in bank l: no shared-memory bank conflicts.
 constexpr int kBpTile = 16;
 constexpr int kBpStrip = 8;
-constexpr int kBpPitch = kBpTile + 1;  // padded row of the shared accumulators
 constexpr int kBpThreads = 32 * kBpGroups;
+static_assert(kBpTile * kBpTile == 32 * kBpStrip, "a warp's 32 strips cover the tile");
 
-struct BpTileAcc {  // [view group][0: x-major, 1: y-major][row * kBpPitch + column]
-    float a[kBpGroups][2][kBpTile * kBpPitch];
+struct BpTileAcc {  // [view group][0: x-major, 1: y-major][strip pixel d][lane]
+    float a[kBpGroups][2][kBpStrip][32];
 };
 
 // Channel window of a strip of pixels whose centres run from (pxa, pya) to
@@ -222,6 +223,13 @@ __device__ __forceinline__ void strip_window(const Geo2 &g, const View2 &vw, flo
     c1 = min(g.ns - 1, (int)floorf(fmaxf(ca, cb) + hw));
 }
 
+// Adds one ray's row lengths times its residual to the strip pixels it
+// touches: d = (first pixel j) - (first strip index), exact small integer.
+__device__ __forceinline__ void strip_add(float *A, int d, const RowW &w, float val) {
+    if ((unsigned)d < (unsigned)kBpStrip) A[d * 32] = fmaf(w.w0, val, A[d * 32]);
+    if ((unsigned)(d + 1) < (unsigned)kBpStrip) A[(d + 1) * 32] = fmaf(w.w1, val, A[(d + 1) * 32]);
+}
+
 // Back-projection of the tile with lower corner (tx0, ty0) over views
 // [0, nv) into S (thread t in [0, kBpThreads)); the caller synchronises the
 // block before reading S with bp_tile_total.
@@ -230,16 +238,11 @@ __device__ __forceinline__ void bp_tile_strips(const Geo2 &g, const float *__res
                                                BpTileAcc &S) {
     const int grp = t >> 5, lane = t & 31;
     const int u = lane & (kBpTile - 1), s0 = (lane / kBpTile) * kBpStrip;
-    const int lv0 = bp_group_begin(nv, grp), lv1 = bp_group_begin(nv, grp + 1);
 #pragma unroll 1
     for (int ax = 0; ax < 2; ++ax) {
-        float *A = S.a[grp][ax];
-        // accumulator of strip pixel d: x-major rays (vertical strip): row s0 + d
-        // of column u; y-major rays (horizontal strip): column s0 + d of row u
-        const int base = ax ? u * kBpPitch + s0 : s0 * kBpPitch + u;
-        const int step = ax ? 1 : kBpPitch;
+        float *A = &S.a[grp][ax][0][lane];
 #pragma unroll
-        for (int d = 0; d < kBpStrip; ++d) A[base + d * step] = 0.f;
+        for (int d = 0; d < kBpStrip; ++d) A[d * 32] = 0.f;
         const int ia = (ax ? ty0 : tx0) + u;   // major row of the rays
         const int jb0 = (ax ? tx0 : ty0) + s0;  // first minor index of the strip
         const int Na = ax ? g.ny : g.nx, Nb = ax ? g.nx : g.ny;
@@ -254,7 +257,7 @@ __device__ __forceinline__ void bp_tile_strips(const Geo2 &g, const float *__res
         const float half_len = 0.5f * (float)(jb1 - jb0) * pb;
         const float ia2 = (float)(2 * ia + 1), iah = (float)ia + 0.5f;
         const float jbf = (float)jb0;
-        for (int lv = lv0; lv < lv1; ++lv) {
+        for (int lv = grp; lv < nv; lv += kBpGroups) {
             const int v = __ldg(views + lv);
             if ((unsigned)v >= (unsigned)g.nviews) continue;  // caller-supplied view out of range
             const View2 vw = g.views[v];
@@ -270,27 +273,21 @@ __device__ __forceinline__ void bp_tile_strips(const Geo2 &g, const float *__res
             const float *rv = r + (size_t)lv * g.ns;
             for (int c = c0; c <= c1; ++c) {
                 const RowW w = row_weights(rr[c], ia2, iah);
-                const float val = __ldg(rv + c);
-                const int d = (int)__fsub_rn(w.j, jbf);  // exact: both are small integers
-                if ((unsigned)d < (unsigned)kBpStrip) {
-                    float &p = A[base + d * step];
-                    p = fmaf(w.w0, val, p);
-                }
-                if ((unsigned)(d + 1) < (unsigned)kBpStrip) {
-                    float &p = A[base + (d + 1) * step];
-                    p = fmaf(w.w1, val, p);
-                }
+                strip_add(A, (int)__fsub_rn(w.j, jbf), w, __ldg(rv + c));
             }
         }
     }
 }
 
-// A'r at tile pixel (px, py) from the accumulators, in the fixed order.
+// A'r at tile pixel (px, py) from the accumulators, in the fixed order: the
+// pixel is strip pixel py mod 8 of lane px + 16 (py / 8) for the x-major
+// rays and strip pixel px mod 8 of lane py + 16 (px / 8) for the y-major rays.
 __device__ __forceinline__ float bp_tile_total(const BpTileAcc &S, int px, int py) {
-    const int i = py * kBpPitch + px;
+    const int lx = px + kBpTile * (py / kBpStrip), dx_ = py % kBpStrip;
+    const int ly = py + kBpTile * (px / kBpStrip), dy_ = px % kBpStrip;
     float acc = 0.f;
 #pragma unroll
-    for (int k = 0; k < kBpGroups; ++k) acc += S.a[k][0][i] + S.a[k][1][i];
+    for (int k = 0; k < kBpGroups; ++k) acc += S.a[k][0][dx_][lx] + S.a[k][1][dy_][ly];
     return acc;
 }
 
