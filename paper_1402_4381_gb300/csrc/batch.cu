@@ -4,7 +4,7 @@
 // covering all scans still running:
 //   1. update   (tiles of every scan's image)      x+ = SQS step (Sec. IV-A)
 //   2. forward  (groups of rays of every scan's next subset)  r = M W (A x+ - y)
-//   3. back-proj(tiles)  zeta+ = A' r, g+, per-tile restart-indicator partials
+//   3. back-proj(16x16 tiles)  zeta+ = A' r, g+, per-tile restart-indicator partials
 //   4. finish   (one block per scan)  xi, l, rho_l (Sec. III-B), in a fixed order
 // The per-scan arithmetic is the single-problem code (proj2d.cuh), so with
 // the default launch shape a batched scan is bit-identical to the same scan
@@ -155,34 +155,42 @@ __global__ void __launch_bounds__(256) batch_forward_kernel(const SliceDesc *__r
     }
 }
 
-template <int TX, int TY>
-__global__ void __launch_bounds__(256) batch_backproject_kernel(const SliceDesc *__restrict__ S, int n, int step) {
+// Back-projection tiles of every scan: the single-problem tile code
+// (bp_tile_strips, same tiles and summation order), then the split-gradient
+// update and the tile's restart-indicator partial.
+__global__ void __launch_bounds__(kBpThreads, 8) batch_backproject_kernel(const SliceDesc *__restrict__ S, int n,
+                                                                       int step) {
     __shared__ int pre[kMaxSlices + 1];
     __shared__ double red[32];
-    const int total = work_prefix(S, n, step, [](const SliceDesc &d) { return slice_tiles<TX, TY>(d); }, pre);
+    __shared__ BpTileAcc acc;
+    const int total =
+        work_prefix(S, n, step, [](const SliceDesc &d) { return slice_tiles<kBpTile, kBpTile>(d); }, pre);
     const int tid = threadIdx.x;
     for (int item = blockIdx.x; item < total; item += gridDim.x) {
         const int s = find_slice(pre, n, item);
         const SliceDesc &d = S[s];
         const int t = item - pre[s];
-        const int ntx = (d.geo.nx + TX - 1) / TX;
-        const int ix = (t % ntx) * TX + tid % TX, iy = (t / ntx) * TY + tid / TX;
-        const bool valid = ix < d.geo.nx && iy < d.geo.ny;
+        const int ntx = (d.geo.nx + kBpTile - 1) / kBpTile;
+        const int tx0 = (t % ntx) * kBpTile, ty0 = (t / ntx) * kBpTile;
         const int next = d.order[(step + 1) % d.M];
-        const float acc = valid ? bp_pixel_sum(d.geo, d.r, d.views + d.off[next], d.cnt[next], ix, iy) : 0.f;
+        bp_tile_strips(d.geo, d.r, d.views + d.off[next], d.cnt[next], tx0, ty0, tid, acc);
+        __syncthreads();
+        const int px = tid % kBpTile, py = tid / kBpTile;
+        const int ix = tx0 + px, iy = ty0 + py;
         double xi_local = 0.0;
-        if (valid) {
+        if (ix < d.geo.nx && iy < d.geo.ny) {
+            const float v = bp_tile_total(acc, px, py);
             const size_t p = (size_t)iy * d.geo.nx + ix;
             const double rho = d.ua.state->rho;
             const float a = (float)(rho / (rho + 1.0));
             const float b = (float)(1.0 / (rho + 1.0));
             const float z_old = d.ua.zeta[p];
             const float g_old = d.ua.g[p];
-            d.ua.zeta[p] = acc;
-            d.ua.g[p] = a * acc + b * g_old;
-            xi_local = (double)(g_old - acc) * (double)(acc - z_old);
+            d.ua.zeta[p] = v;
+            d.ua.g[p] = a * v + b * g_old;
+            xi_local = (double)(g_old - v) * (double)(v - z_old);
         }
-        const double bs = block_sum2d(xi_local, red);
+        const double bs = block_sum2d(xi_local, red);  // ends with a barrier: acc is free again
         if (tid == 0) d.ua.partials[t] = bs;
     }
 }
@@ -195,7 +203,7 @@ __global__ void __launch_bounds__(256) batch_finish_kernel(const SliceDesc *__re
         if (!slice_active(d, step)) continue;
         UpdateArgs ua = d.ua;
         ua.subset = d.order[(step + 1) % d.M];
-        finish_subset_iteration(ua, slice_tiles<TX, TY>(d));
+        finish_subset_iteration(ua, slice_tiles<kBpTile, kBpTile>(d));
         __syncthreads();
     }
 }
@@ -224,7 +232,7 @@ template <int TX, int TY, int LANES>
 int launch_step(const oslalm_batch *b, int step, int grid_upd, int grid_fp, int grid_bp, cudaStream_t st) {
     batch_update_kernel<TX, TY><<<grid_upd, 256, 0, st>>>(b->d, b->n, step);
     batch_forward_kernel<LANES><<<grid_fp, 256, 0, st>>>(b->d, b->n, step);
-    batch_backproject_kernel<TX, TY><<<grid_bp, 256, 0, st>>>(b->d, b->n, step);
+    batch_backproject_kernel<<<grid_bp, kBpThreads, 0, st>>>(b->d, b->n, step);
     batch_finish_kernel<TX, TY><<<std::min(b->n, 4096), 256, 0, st>>>(b->d, b->n, step);
     OSL_LAUNCH_CHECK("batch step");
     return OSLALM_OK;
@@ -235,7 +243,7 @@ int grid_sizes(const oslalm_batch *b, int &gu, int &gf, int &gb) {
     int ou = 0, of = 0, ob = 0;
     OSL_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ou, batch_update_kernel<TX, TY>, 256, 0));
     OSL_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&of, batch_forward_kernel<LANES>, 256, 0));
-    OSL_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ob, batch_backproject_kernel<TX, TY>, 256, 0));
+    OSL_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ob, batch_backproject_kernel, kBpThreads, 0));
     auto pick = [&](int occ) {
         int per = b->blocks_per_sm > 0 ? std::min(b->blocks_per_sm, std::max(occ, 1)) : std::max(occ, 1);
         return b->num_sms * per;

@@ -190,14 +190,6 @@ __device__ __forceinline__ RowW row_weights(const RayP &r, float ia2, float iah)
     return w;
 }
 
-// length of ray r in pixel (ix, iy)
-__device__ __forceinline__ float chord2(const RayP &r, float ixf, float iyf) {
-    const float ia = r.axis ? iyf : ixf;
-    const float jb = r.axis ? ixf : iyf;
-    const RowW w = row_weights(r, __fmaf_rn(2.f, ia, 1.f), __fadd_rn(ia, 0.5f));
-    const float d = __fsub_rn(jb, w.j);
-    return d == 0.f ? w.w0 : (d == 1.f ? w.w1 : 0.f);
-}
 
 // ---------------------------------------------------------------- projector launchers
 enum FpMode { FP_PLAIN = 0, FP_RESID = 1 };

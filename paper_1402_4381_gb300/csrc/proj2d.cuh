@@ -74,101 +74,14 @@ __device__ __forceinline__ float atan_unit(float t) {
     return p * t;
 }
 
-// channel window of pixel centre (px, py) in view vw: channels whose ray may
-// cross the pixel, widened by a margin far above the rounding of the ray
-// tables and the error of the angle evaluation, so that no channel with a
-// non-zero length is missed.
-__device__ __forceinline__ void channel_window(const Geo2 &g, const View2 &vw, float px, float py, int &c0,
-                                               int &c1) {
-    float cc, hw;
-    if (g.kind == OSLALM_PAR2D) {
-        constexpr float kMargin = 0.02f;
-        float s = -px * vw.su + py * vw.cu;
-        cc = s * g.inv_ds + g.c0;
-        hw = 0.5f * (g.dx * fabsf(vw.su) + g.dy * fabsf(vw.cu)) * g.inv_ds + kMargin;
-    } else {
-        float a = px * vw.cu + py * vw.su + g.dso;  // along u from the source
-        float b = -px * vw.su + py * vw.cu;         // along e
-        // fast form when |b| <= a for every pixel: angle error < 2.5e-6 rad
-        const float gam = g.fast_atan ? atan_unit(__fdividef(b, a)) : atan2f(b, a);
-        const float kMargin = 0.02f + 2.5e-6f * g.dsd * g.inv_ds;
-        float d2 = a * a + b * b - g.half_diag * g.half_diag;
-        float ang = g.half_diag * rsqrtf(fmaxf(d2, 1e-12f));  // >= angular radius of the pixel
-        cc = gam * g.dsd * g.inv_ds + g.c0;
-        hw = ang * 1.0001f * g.dsd * g.inv_ds + kMargin;
-    }
-    c0 = max(0, (int)ceilf(cc - hw));
-    c1 = min(g.ns - 1, (int)floorf(cc + hw));
-}
-
-// pixel indices as exact floats for the length arithmetic
-struct PixF {
-    float x2, xh, xf, y2, yh, yf;  // 2 i + 1, i + 1/2, i for i = ix, iy
-};
-
-__device__ __forceinline__ PixF pix_f(int ix, int iy) {
-    PixF p;
-    p.xf = (float)ix;
-    p.yf = (float)iy;
-    p.x2 = __fmaf_rn(2.f, p.xf, 1.f);
-    p.y2 = __fmaf_rn(2.f, p.yf, 1.f);
-    p.xh = __fadd_rn(p.xf, 0.5f);
-    p.yh = __fadd_rn(p.yf, 0.5f);
-    return p;
-}
-
-// length of ray r in the pixel (same arithmetic as chord2)
-__device__ __forceinline__ float chord_px(const RayP &r, const PixF &p) {
-    const bool ay = r.axis != 0;
-    const RowW w = row_weights(r, ay ? p.y2 : p.x2, ay ? p.yh : p.xh);
-    const float d = __fsub_rn(ay ? p.xf : p.yf, w.j);
-    return d == 0.f ? w.w0 : (d == 1.f ? w.w1 : 0.f);
-}
-
 // The back-projected value of a pixel is summed in a fixed order: the views
 // are dealt to kBpGroups groups (list position lv goes to group lv mod
 // kBpGroups); within a group the contributions of the x-major rays (views in
 // list order, channels ascending) and of the y-major rays (same order) are
 // summed separately, by fused multiply-adds, and added; the group totals are
-// added in group order.  The tiled kernel and the pixel-by-pixel function
-// below follow this order, so they give the same bits.
+// added in group order.  The single-problem and the batched kernels both run
+// bp_tile_strips, so they give the same bits.
 constexpr int kBpGroups = 8;
-
-// Sum over the views of group k of length x r for the rays crossing pixel
-// (ix, iy), in the order above.
-__device__ __forceinline__ float bp_pixel_group(const Geo2 &g, const float *__restrict__ r,
-                                                const int *__restrict__ views, int nv, int k, int ix, int iy) {
-    float accx = 0.f, accy = 0.f;
-    const float px = g.xlo + ((float)ix + 0.5f) * g.dx;
-    const float py = g.ylo + ((float)iy + 0.5f) * g.dy;
-    const PixF pf = pix_f(ix, iy);
-    for (int lv = k; lv < nv; lv += kBpGroups) {
-        const int v = __ldg(views + lv);
-        if ((unsigned)v >= (unsigned)g.nviews) continue;  // caller-supplied view out of range
-        const View2 vw = g.views[v];
-        int c0, c1;
-        channel_window(g, vw, px, py, c0, c1);
-        const RayP *rr = g.rays + (size_t)v * g.ns;
-        const float *rv = r + (size_t)lv * g.ns;
-        for (int c = c0; c <= c1; ++c) {
-            const RayP rp = rr[c];
-            const float t = chord_px(rp, pf);
-            const float val = __ldg(rv + c);
-            if (rp.axis) accy = fmaf(t, val, accy);
-            else accx = fmaf(t, val, accx);
-        }
-    }
-    return accx + accy;
-}
-
-// A'r at pixel (ix, iy) over the listed views, in the order above.
-__device__ __forceinline__ float bp_pixel_sum(const Geo2 &g, const float *__restrict__ r,
-                                              const int *__restrict__ views, int nv, int ix, int iy) {
-    float acc = 0.f;
-#pragma unroll
-    for (int k = 0; k < kBpGroups; ++k) acc += bp_pixel_group(g, r, views, nv, k, ix, iy);
-    return acc;
-}
 
 // ---------------------------------------------------------------- tiled back-projection
 // A tile of kBpTile x kBpTile pixels is back-projected by 32 x kBpGroups
@@ -195,8 +108,11 @@ struct BpTileAcc {  // [view group][0: x-major, 1: y-major][strip pixel d][lane]
 // any pixel of it.  The channel coordinate of a point is linear (parallel
 // beam) or monotone (fan: the angle seen from the source) along a segment,
 // so the end pixels span the centres; the half-width takes the smallest
-// distance from the source that any point of the segment can have.  Margins
-// as in channel_window.
+// distance from the source that any point of the segment can have, and the
+// circumradius of a pixel.  The window is widened by a margin far above the
+// rounding of the ray tables and the error of the angle evaluation (fan:
+// atan_unit, < 2.5e-6 rad, when every pixel centre is within 45 degrees of
+// the source's axis), so that no channel with a non-zero length is missed.
 __device__ __forceinline__ void strip_window(const Geo2 &g, const View2 &vw, float pxa, float pya, float pxb,
                                              float pyb, float half_len, int &c0, int &c1) {
     float ca, cb, hw;
