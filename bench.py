@@ -31,6 +31,11 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "A/A' subset-iters/s (OS-LALM, 2D fan beam 512^2, 984x888, M=24)"
+
+# DRAM bytes (read + write) per launch of the fan-beam workload's kernels, from
+# one ncu --set full capture of the current kernels on this bench's warm-up
+# launches (cold caches); to be re-taken whenever a kernel changes.
+NCU_DRAM_BYTES_FAN = {"bp2d_kernel": 3.45e6, "fp2d_kernel": 2.44e6, "update2d_kernel": 3.68e6}
 UNIT = "subset-iters/s"
 
 
@@ -326,7 +331,9 @@ def run_ours(args):
         achieved = ops / (per[dom] / 1000.0)
         roof = {"kernel": {"forward": "fp2d_kernel", "backproject": "bp2d_kernel"}[dom], "bound": "alu",
                 "achieved": achieved / 1e12, "peak": peak_ops / 1e12, "unit": "TFLOP/s",
-                "frac": achieved / peak_ops, "traffic": None,
+                "frac": achieved / peak_ops,
+                "traffic": NCU_DRAM_BYTES_FAN.get({"forward": "fp2d_kernel", "backproject": "bp2d_kernel"}[dom])
+                if args.workload == "fan" else None,
                 "work_per_launch": f"{inter:.4g} intersections x 3 FP32 ops",
                 "peak_basis": f"152 SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz (median SM clock under load)"}
     else:
@@ -335,7 +342,8 @@ def run_ours(args):
         achieved = traffic / (per[dom] / 1000.0)
         hbm = (pk or {}).get("hbm_gbs", 6800.0) * 1e9
         roof = {"kernel": "update3d_kernel" if g.kind == 2 else "update2d_kernel", "bound": "hbm", "achieved": achieved / 1e9, "peak": hbm / 1e9,
-                "unit": "GB/s", "frac": achieved / hbm, "traffic": None}
+                "unit": "GB/s", "frac": achieved / hbm,
+                "traffic": NCU_DRAM_BYTES_FAN["update2d_kernel"] if args.workload == "fan" else None}
     roof["per_kernel_ms"] = {k: round(v, 5) for k, v in per.items()}
 
     # ---- time to 1 HU against a converged image (M = 1 continuation, long run)
