@@ -47,11 +47,14 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-time-to-hu", action="store_true")
-    ap.add_argument("--workload", default="fan", choices=["fan", "cone", "parallel", "batch"],
-                    help="fan: the 512^2 fan-beam scan (default, the headline); cone / parallel: the "
-                         "512x512x128 cone-beam and 128^2 parallel-beam scans; batch: 64 fan-beam slices "
-                         "of mixed sizes advanced together")
+    ap.add_argument("--workload", default="fan", choices=["fan", "fan256", "cone", "parallel", "batch"],
+                    help="fan: the 512^2 fan-beam scan (default, the headline); fan256: the same scan family at "
+                         "256^2, 492 views, M = 12; cone / parallel: the 512x512x128 cone-beam and 128^2 "
+                         "parallel-beam scans; batch: 64 fan-beam slices of mixed sizes advanced together")
     ap.add_argument("--slices", type=int, default=64)
+    ap.add_argument("--matrix", action="store_true",
+                    help="2D: stream the system matrix held in device memory (oslalm_geom_build_matrix) instead "
+                         "of evaluating the projector's lengths in every launch")
     return ap.parse_args()
 
 
@@ -192,7 +195,7 @@ def run_reference(args):
     if rank != 0:
         return 0
     from paper_1402_4381_gb300 import workloads as W
-    wl = {"fan": W.c1_fan, "cone": W.c2_cone, "parallel": W.c0_parallel}[args.workload]()
+    wl = {"fan": W.c1_fan, "fan256": W.c1_fan_256, "cone": W.c2_cone, "parallel": W.c0_parallel}[args.workload]()
     scan = wl.make_scan()
     from oracle import fbp as ofbp
     x0 = np.maximum(ofbp.fbp(wl.geom, scan["y"].astype(np.float64)), 0.0)
@@ -225,7 +228,7 @@ def run_ours(args):
         torch.cuda.set_device(0)
     from paper_1402_4381_gb300 import oslalm, workloads as W
 
-    wl = {"fan": W.c1_fan, "cone": W.c2_cone, "parallel": W.c0_parallel}[args.workload]()
+    wl = {"fan": W.c1_fan, "fan256": W.c1_fan_256, "cone": W.c2_cone, "parallel": W.c0_parallel}[args.workload]()
     if world > 1:  # independent replicas: a different noise realisation per rank
         wl.noise_seed += 1000 * rank
     g = wl.geom
@@ -235,6 +238,13 @@ def run_ours(args):
     y = torch.as_tensor(scan["y"], device=dev)
     w = torch.as_tensor(scan["w"], device=dev)
     geom = oslalm.Geometry(g)
+    matrix = None
+    if g.kind != 2 and args.matrix:  # set-up: the system matrix held in device memory
+        t0 = time.perf_counter()
+        geom.build_matrix()
+        torch.cuda.synchronize()
+        matrix = {"forward_bytes": geom.matrix_bytes[0], "backprojection_bytes": geom.matrix_bytes[1],
+                  "build_s": round(time.perf_counter() - t0, 3)}
     # initial image: FBP of the log sinogram, clipped to x >= 0 (set-up)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
@@ -325,7 +335,26 @@ def run_ours(args):
     pk = peaks()
     inter = intersections_per_subset(g, wl.M)
     sm_mhz = clocks.get("sm_mhz") or 2070.0
-    if dom in ("forward", "backproject"):
+    if dom in ("forward", "backproject") and matrix:
+        # the stored lengths of one subset (its share of the layout) plus the
+        # sinogram and image data the kernel reads and writes
+        nvs = g.nviews / wl.M
+        rays = nvs * g.ns * g.nt
+        npix = g.nx * g.ny * g.nz
+        wb = 4 if wl.w_dtype == "f32" else 2
+        if dom == "forward":
+            nbytes = matrix["forward_bytes"] * nvs / g.nviews + rays * (4 + wb + 4) + 4 * npix
+            kname = "fp2d_table_kernel"
+        else:
+            nbytes = matrix["backprojection_bytes"] * nvs / g.nviews + rays * 4 + 16 * npix
+            kname = "bp2d_kernel (matrix)"
+        achieved = nbytes / (per[dom] / 1000.0)
+        hbm = (pk or {}).get("hbm_gbs", 6800.0) * 1e9
+        roof = {"kernel": kname, "bound": "hbm", "achieved": achieved / 1e9, "peak": hbm / 1e9, "unit": "GB/s",
+                "frac": achieved / hbm, "traffic": NCU_DRAM_BYTES_FAN.get(kname) if args.workload == "fan" else None,
+                "work_per_launch": f"{nbytes / 1e6:.1f} MB (stored lengths of one subset, sinogram and image data)",
+                "intersections_per_s": inter / (per[dom] / 1000.0)}
+    elif dom in ("forward", "backproject"):
         ops = 3.0 * inter  # FP32 ops per (ray, pixel) pair: crossing, length, multiply-accumulate
         peak_ops = 152 * 128 * sm_mhz * 1e6
         achieved = ops / (per[dom] / 1000.0)
@@ -358,7 +387,8 @@ def run_ours(args):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": wl.name, "image": [g.nx, g.ny], "views": g.nviews, "channels": g.ns, "M": wl.M,
                    "iterations_per_step": wl.n_iter, "storage": {"W": wl.w_dtype, "D": wl.d_dtype},
-                   "parallelism": f"replicas{world}", "l2": "flushed between timed steps (256 MB write)"},
+                   "parallelism": f"replicas{world}", "l2": "flushed between timed steps (256 MB write)",
+                   "system_matrix": matrix or "evaluated in every launch"},
         "gpu_launches": args.steps * (wl.n_iter * wl.M * 3 + 3),
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "roofline": roof, "clocks": clocks,

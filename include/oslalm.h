@@ -47,6 +47,7 @@
 #ifndef OSLALM_H
 #define OSLALM_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -134,6 +135,26 @@ int oslalm_version(void);
  * Errors: ARG (bad descriptor), ALLOC, CUDA.  *out is NULL on failure. */
 int oslalm_geom_create(const oslalm_geom_desc *desc, oslalm_geom **out);
 int oslalm_geom_destroy(oslalm_geom *g);
+
+/* The system matrix A of Sec. IV (the exact ray/pixel lengths that the
+ * projector pair evaluates) held in device memory, for 2D geometries: every
+ * (ray, major row) length pair, evaluated once by the projector's own
+ * arithmetic and stored in one layout per direction.  Afterwards
+ * oslalm_project, oslalm_backproject and the OS-LALM calls on this geometry
+ * stream the stored lengths instead of evaluating them, with bit-identical
+ * results.  Owned by the geometry (freed by oslalm_geom_drop_matrix or
+ * oslalm_geom_destroy); bytes[host, 2] (may be NULL) receives the sizes of the
+ * forward and the back-projection layouts (together about 8 GB for 512^2
+ * pixels, 984 views x 888 channels).  Build it before
+ * creating problems whose iterations are captured in CUDA graphs (a graph
+ * keeps the kernels it was captured with).  Synchronises `stream` (cudaStream_t,
+ * NULL = legacy default).  Errors: ARG (NULL handle, 3D geometry), RANGE
+ * (more than 65535 views or 2^32 entries, or a geometry outside the layout's
+ * assumptions: then no matrix is kept and the evaluating kernels stay in
+ * use), ALLOC, CUDA.
+ * oslalm_geom_drop_matrix synchronises the device and frees the matrix. */
+int oslalm_geom_build_matrix(oslalm_geom *g, size_t *bytes, void *stream);  /* bytes[2] */
+int oslalm_geom_drop_matrix(oslalm_geom *g);
 
 /* Host-only view of the 2D system model: the per-ray parameters that the
  * projector pair reads for view `view` (arrays [host, ns] each).  Ray c is

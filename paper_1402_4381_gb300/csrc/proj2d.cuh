@@ -146,6 +146,56 @@ __device__ __forceinline__ void strip_add(float *A, int d, const RowW &w, float 
     if ((unsigned)(d + 1) < (unsigned)kBpStrip) A[(d + 1) * 32] = fmaf(w.w1, val, A[(d + 1) * 32]);
 }
 
+// The strip of lane `lane` for the rays of orientation ax (0: x-major,
+// 1: y-major) in the tile with lower corner (tx0, ty0): its major row ia (as
+// the exact floats 2 ia + 1 and ia + 1/2), its first minor index jb0, and the
+// centres (mm) of its first and last pixel inside the image.
+struct StripCtx {
+    float ia2, iah, jbf;
+    float pxa, pya, pxb, pyb, half_len;
+    bool valid;
+};
+
+__device__ __forceinline__ StripCtx strip_ctx(const Geo2 &g, int ax, int tx0, int ty0, int lane) {
+    StripCtx s;
+    const int u = lane & (kBpTile - 1), s0 = (lane / kBpTile) * kBpStrip;
+    const int ia = (ax ? ty0 : tx0) + u;   // major row of the rays
+    const int jb0 = (ax ? tx0 : ty0) + s0;  // first minor index of the strip
+    const int Na = ax ? g.ny : g.nx, Nb = ax ? g.nx : g.ny;
+    s.valid = ia < Na && jb0 < Nb;
+    const int jb1 = min(jb0 + kBpStrip, Nb) - 1;
+    const float pa = ax ? g.dy : g.dx, pb = ax ? g.dx : g.dy;
+    const float am = (ax ? g.ylo : g.xlo) + ((float)ia + 0.5f) * pa;  // major coordinate (mm)
+    const float blo = (ax ? g.xlo : g.ylo) + ((float)jb0 + 0.5f) * pb;
+    const float bhi = (ax ? g.xlo : g.ylo) + ((float)jb1 + 0.5f) * pb;
+    s.pxa = ax ? blo : am;
+    s.pya = ax ? am : blo;
+    s.pxb = ax ? bhi : am;
+    s.pyb = ax ? am : bhi;
+    s.half_len = 0.5f * (float)(jb1 - jb0) * pb;
+    s.ia2 = (float)(2 * ia + 1);
+    s.iah = (float)ia + 0.5f;
+    s.jbf = (float)jb0;
+    return s;
+}
+
+// Candidate channels [c0, c1] of view vw for the strip (rays of orientation
+// ax only); c0 > c1 when there are none.
+__device__ __forceinline__ void strip_channels(const Geo2 &g, const View2 &vw, int ax, const StripCtx &s, int &c0,
+                                               int &c1) {
+    int k0 = 0, k1 = g.ns;  // channels of this view whose rays have this orientation
+    if (vw.axis0 == ax) k1 = vw.split;
+    else k0 = vw.split;
+    if (k0 >= k1) {
+        c0 = 0;
+        c1 = -1;
+        return;
+    }
+    strip_window(g, vw, s.pxa, s.pya, s.pxb, s.pyb, s.half_len, c0, c1);
+    c0 = max(c0, k0);
+    c1 = min(c1, k1 - 1);
+}
+
 // Back-projection of the tile with lower corner (tx0, ty0) over views
 // [0, nv) into S (thread t in [0, kBpThreads)); the caller synchronises the
 // block before reading S with bp_tile_total.
@@ -153,43 +203,79 @@ __device__ __forceinline__ void bp_tile_strips(const Geo2 &g, const float *__res
                                                const int *__restrict__ views, int nv, int tx0, int ty0, int t,
                                                BpTileAcc &S) {
     const int grp = t >> 5, lane = t & 31;
-    const int u = lane & (kBpTile - 1), s0 = (lane / kBpTile) * kBpStrip;
 #pragma unroll 1
     for (int ax = 0; ax < 2; ++ax) {
         float *A = &S.a[grp][ax][0][lane];
 #pragma unroll
         for (int d = 0; d < kBpStrip; ++d) A[d * 32] = 0.f;
-        const int ia = (ax ? ty0 : tx0) + u;   // major row of the rays
-        const int jb0 = (ax ? tx0 : ty0) + s0;  // first minor index of the strip
-        const int Na = ax ? g.ny : g.nx, Nb = ax ? g.nx : g.ny;
-        if (ia >= Na || jb0 >= Nb) continue;
-        const int jb1 = min(jb0 + kBpStrip, Nb) - 1;
-        const float pa = ax ? g.dy : g.dx, pb = ax ? g.dx : g.dy;
-        const float am = (ax ? g.ylo : g.xlo) + ((float)ia + 0.5f) * pa;  // major coordinate (mm)
-        const float blo = (ax ? g.xlo : g.ylo) + ((float)jb0 + 0.5f) * pb;
-        const float bhi = (ax ? g.xlo : g.ylo) + ((float)jb1 + 0.5f) * pb;
-        const float pxa = ax ? blo : am, pya = ax ? am : blo;
-        const float pxb = ax ? bhi : am, pyb = ax ? am : bhi;
-        const float half_len = 0.5f * (float)(jb1 - jb0) * pb;
-        const float ia2 = (float)(2 * ia + 1), iah = (float)ia + 0.5f;
-        const float jbf = (float)jb0;
+        const StripCtx sc = strip_ctx(g, ax, tx0, ty0, lane);
+        if (!sc.valid) continue;
         for (int lv = grp; lv < nv; lv += kBpGroups) {
             const int v = __ldg(views + lv);
             if ((unsigned)v >= (unsigned)g.nviews) continue;  // caller-supplied view out of range
-            const View2 vw = g.views[v];
-            int k0 = 0, k1 = g.ns;  // channels of this view whose rays have this orientation
-            if (vw.axis0 == ax) k1 = vw.split;
-            else k0 = vw.split;
-            if (k0 >= k1) continue;
             int c0, c1;
-            strip_window(g, vw, pxa, pya, pxb, pyb, half_len, c0, c1);
-            c0 = max(c0, k0);
-            c1 = min(c1, k1 - 1);
+            strip_channels(g, g.views[v], ax, sc, c0, c1);
             const RayP *rr = g.rays + (size_t)v * g.ns;
             const float *rv = r + (size_t)lv * g.ns;
             for (int c = c0; c <= c1; ++c) {
-                const RowW w = row_weights(rr[c], ia2, iah);
-                strip_add(A, (int)__fsub_rn(w.j, jbf), w, __ldg(rv + c));
+                const RowW w = row_weights(rr[c], sc.ia2, sc.iah);
+                strip_add(A, (int)__fsub_rn(w.j, sc.jbf), w, __ldg(rv + c));
+            }
+        }
+    }
+}
+
+constexpr int kBpPrefetch = 8;  // stored entries in flight per lane (memory latency)
+
+// The same back-projection read from the device system matrix (Geo2): the
+// tile's lengths stream from memory instead of being evaluated, in the same
+// order per accumulator (views in list order, channels ascending), so the
+// result is bit-identical to bp_tile_strips.  tile = the tile's index in
+// row-major tile order.
+__device__ __forceinline__ void bp_tile_table(const Geo2 &g, const float *__restrict__ r,
+                                              const int *__restrict__ views, int nv, int tile, int t, BpTileAcc &S) {
+    const int grp = t >> 5, lane = t & 31;
+    const size_t ntiles = (size_t)((g.nx + kBpTile - 1) / kBpTile) * ((g.ny + kBpTile - 1) / kBpTile);
+#pragma unroll
+    for (int ax = 0; ax < 2; ++ax)
+#pragma unroll
+        for (int d = 0; d < kBpStrip; ++d) S.a[grp][ax][d][lane] = 0.f;
+    for (int lv = grp; lv < nv; lv += kBpGroups) {
+        const int v = __ldg(views + lv);
+        if ((unsigned)v >= (unsigned)g.nviews) continue;  // caller-supplied view out of range
+        const float *rv = r + (size_t)lv * g.ns;
+#pragma unroll 1
+        for (int ax = 0; ax < 2; ++ax) {
+            const size_t blk = ((size_t)v * 2 + ax) * ntiles + tile;
+            const uint2 b = __ldg(g.bp_blk + blk);
+            if (b.y == 0) continue;
+            const unsigned h = __ldg(g.bp_hdr + blk * 32 + lane);
+            const int cnt = (int)(h >> 24);
+            const int dir = (h >> 20) & 1u ? -1 : 1;
+            int d = (int)((h >> 16) & 15u) - 1;
+            const float *rc = rv + (h & 0xffffu);
+            const uint2 *E = g.bp_ent + (size_t)b.x * 32 + lane;
+            float *A = &S.a[grp][ax][0][lane];
+            // kBpPrefetch entries (and residuals) in flight per lane, then
+            // added in channel order
+            for (int i0 = 0; i0 < cnt; i0 += kBpPrefetch) {
+                uint2 e[kBpPrefetch];
+                float val[kBpPrefetch];
+#pragma unroll
+                for (int k = 0; k < kBpPrefetch; ++k) {
+                    const bool ok = i0 + k < cnt;
+                    e[k] = ok ? __ldg(E + (size_t)(i0 + k) * 32) : make_uint2(0u, 0u);
+                    val[k] = ok ? __ldg(rc + i0 + k) : 0.f;
+                }
+#pragma unroll
+                for (int k = 0; k < kBpPrefetch; ++k) {
+                    if (i0 + k >= cnt) break;
+                    d += dir * (int)((e[k].x >> 31) | ((e[k].y >> 31) << 1));
+                    RowW w;
+                    w.w0 = __uint_as_float(e[k].x & 0x7fffffffu);
+                    w.w1 = __uint_as_float(e[k].y & 0x7fffffffu);
+                    strip_add(A, d, w, val[k]);
+                }
             }
         }
     }

@@ -91,6 +91,8 @@ def lib():
         "oslalm_profile_iterate": ([_VP, _VP, i, ctypes.POINTER(d), ip, _VP], i),
         "oslalm_fbp": ([_VP, _VP, _VP, i, _VP], i),
         "oslalm_ray_table": ([ctypes.POINTER(GeomDesc), i, _VP, _VP, _VP, _VP], i),
+        "oslalm_geom_build_matrix": ([_VP, _VP, _VP], i),
+        "oslalm_geom_drop_matrix": ([_VP], i),
         "oslalm_batch_create": ([ctypes.POINTER(_VP), i, ctypes.POINTER(_VP)], i),
         "oslalm_batch_destroy": ([_VP], i),
         "oslalm_batch_iterate": ([_VP, ctypes.POINTER(_VP), i, i, _VP], i),
@@ -229,6 +231,18 @@ class Geometry:
         _check(lib().oslalm_backproject(self._h, _ptr(sino), _ptr(out), _ptr(vt), nv, int(accumulate),
                                         _stream(stream)), "backproject")
         return out
+
+    def build_matrix(self, stream=None) -> int:
+        """Hold the 2D system matrix in device memory (oslalm_geom_build_matrix);
+        returns its size in bytes (self.matrix_bytes: forward and
+        back-projection layouts)."""
+        n = (ctypes.c_size_t * 2)()
+        _check(lib().oslalm_geom_build_matrix(self._h, n, _stream(stream)), "geom_build_matrix")
+        self.matrix_bytes = (int(n[0]), int(n[1]))
+        return sum(self.matrix_bytes)
+
+    def drop_matrix(self):
+        _check(lib().oslalm_geom_drop_matrix(self._h), "geom_drop_matrix")
 
     def fbp(self, sino, out=None, clip=True, stream=None):
         """Filtered back-projection of the full sinogram (initial image)."""

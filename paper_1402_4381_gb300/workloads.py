@@ -85,6 +85,13 @@ def c2_cone() -> Workload:
                     w_dtype="bf16")
 
 
+def c1_fan_256() -> Workload:
+    """The fan-beam scan family at 256^2 pixels, 492 views (M = 12 subsets of
+    41 views): one of the batched workload's sizes, and a case small enough
+    for detailed kernel profiling."""
+    return scaled(c1_fan(), 256, 492, 888, 12, name_suffix="256")
+
+
 def scaled(w: Workload, nx: int, nviews: int, ns: int, M: int, name_suffix="small",
            nz: int | None = None, nt: int | None = None) -> Workload:
     """Same scan family at a smaller size (same field of view and fan angles)."""
