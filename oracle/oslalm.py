@@ -38,6 +38,17 @@ Readings (the paper is silent or ambiguous):
 * regularizer R(x) = beta sum_{j<k neighbours} w_jk psi(x_j - x_k) with the
   hyperbola psi(t) = delta^2 (sqrt(1 + (t/delta)^2) - 1), w_jk = 1/(index
   distance), missing neighbours at the border omitted.
+
+Barzilai-Borwein scaling (supplement Sec. II-A, Eqs. secant_eq and
+scale_factor_alpha_k), optional: the majorizer L_diag of the x-update becomes
+H_k = alpha_k L_diag, with alpha_k the weighted least-squares fit of the secant
+equation y_k ~ H_k s_k under P = L_diag^-1 and alpha <= 1:
+    alpha* = s'y / s'L_diag s,  alpha = min(alpha*, 1).
+Readings: as for the restart test (Sec. III-B), the gradients are replaced by
+their subset approximations, so s = x+ - x and y = zeta+ - zeta of each
+subset-iteration, and alpha is refitted at every subset-iteration and used by
+the next x-update; alpha = 1 (the plain majorizer) at the start and whenever
+the fit has no positive curvature (s'y <= 0) or s = 0.
 """
 from __future__ import annotations
 
@@ -240,14 +251,27 @@ def fista_momentum(n: int):
     return out
 
 
+def bb_scale(s, y, D) -> float:
+    """Barzilai-Borwein scale of the majorizer (supplement Eq.
+    scale_factor_alpha_k): argmin_{alpha <= 1} 1/2 ||y - alpha D s||^2_{D^-1},
+    i.e. min(s'y / s'Ds, 1); 1 when s'y <= 0 or s'Ds = 0 (reading)."""
+    num = float(np.sum(s * y))
+    den = float(np.sum(D * s * s))
+    if not (den > 0.0 and num > 0.0):
+        return 1.0
+    return min(num / den, 1.0)
+
+
 class OsLalm:
     """OS-LALM with n inner FISTA steps (n = 1: one projected SQS step),
-    fixed rho or downward continuation."""
+    fixed rho or downward continuation, optional Barzilai-Borwein scaling of
+    the majorizer."""
 
     def __init__(self, data: SubsetData, D, beta: float, delta: float, nbr: int,
                  order: Optional[Sequence[int]] = None, rho_mode: str = "continuation",
                  rho_fixed: float = 1.0, rho_min: float = 1e-3, curvature: str = "huber",
-                 nonneg: bool = True, replay: Optional[Sequence[int]] = None, n_inner: int = 1):
+                 nonneg: bool = True, replay: Optional[Sequence[int]] = None, n_inner: int = 1,
+                 bb: bool = False):
         self.data = data
         self.M = data.M
         self.D = np.asarray(D, dtype=np.float64)
@@ -260,6 +284,8 @@ class OsLalm:
         self.nonneg = nonneg
         self.replay = replay
         self.n_inner = int(n_inner)
+        self.bb = bool(bb)
+        self.alpha = 1.0
         self.history = []
 
     def init(self, x0):
@@ -269,6 +295,7 @@ class OsLalm:
         self.g = self.zeta.copy()
         self.l = 0
         self.rho = 1.0 if self.rho_mode == "continuation" else self.rho_fixed
+        self.alpha = 1.0
 
     def _reg(self, x):
         if self.beta == 0.0:
@@ -287,15 +314,17 @@ class OsLalm:
             grad Phi(v) = grad R(v) + s + rho D (v - x),
             v_{i+1} = u_{i+1} + gamma_i (u_{i+1} - u_i),  u_0 = v_0 = x,
         and returns u_n.  n = 1 is the single projected step
-        x - (s + grad R(x)) / (rho D + D_R(x))."""
+        x - (s + grad R(x)) / (rho D + D_R(x)).  With Barzilai-Borwein
+        scaling, H = alpha D takes the place of D."""
         gam = fista_momentum(self.n_inner)
+        H = self.alpha * self.D
         u_prev, v = x, x
         for i in range(self.n_inner):
             gR, DR = self._reg(v)
             if i == 0:
-                u = x - (s + gR) / (rho * self.D + DR)
+                u = x - (s + gR) / (rho * H + DR)
             else:
-                u = v - (gR + s + rho * self.D * (v - x)) / (rho * self.D + DR)
+                u = v - (gR + s + rho * H * (v - x)) / (rho * H + DR)
             if self.nonneg:
                 u = np.maximum(u, 0.0)
             v = u + gam[i] * (u - u_prev)
@@ -321,7 +350,11 @@ class OsLalm:
                 restart = xi > 0.0
             self.l = 0 if restart else self.l + 1
             self.rho = rho_l(self.l, self.rho_min)
-        self.history.append(dict(j=self.j, rho_used=rho, xi=xi, restart=restart, l=self.l))
+        alpha_used = self.alpha
+        if self.bb:  # secant fit with the subset-gradient approximations
+            self.alpha = bb_scale(x_new - x, zeta_new - zeta, self.D)
+        self.history.append(dict(j=self.j, rho_used=rho, xi=xi, restart=restart, l=self.l,
+                                 alpha_used=alpha_used, alpha=self.alpha))
         self.x, self.g, self.zeta = x_new, g_new, zeta_new
         self.j += 1
 
