@@ -107,6 +107,15 @@ typedef struct oslalm_params {
     int w_dtype;      /* storage of W: OSLALM_F32 | OSLALM_F16 | OSLALM_BF16 */
     int d_dtype;      /* storage of the SQS denominator D: same choices */
     int use_graph;    /* 1: replay whole iterations from a captured CUDA graph */
+    int bb;           /* 1: Barzilai-Borwein scaling of the majorizer (supplement Sec. II-A,
+                         Eqs. secant_eq and scale_factor_alpha_k): the x-updates of
+                         iteration k+1 use H = alpha D in place of D, with alpha =
+                         min(sum_m s_m'y_m / sum_m s_m'D s_m, 1) fitted at the end of
+                         iteration k from each subset's secant pair over that iteration
+                         (s_m = change of the iterate at which subset m's gradient was
+                         taken, y_m = change of that gradient); 1 until pairs exist and
+                         when sum s'y <= 0.  Holds 2 M images of history.  0: plain SQS
+                         majorizer.  Batches take bb = 0 only. */
 } oslalm_params;
 
 /* One record per subset-iteration (filled by oslalm_iterate when asked). */
@@ -117,6 +126,7 @@ typedef struct oslalm_stats {
     int restart;      /* 1 if l was reset */
     int subset;       /* subset whose gradient was computed (sigma(j+1)) */
     int pad;
+    double alpha;     /* Barzilai-Borwein scale after this subset-iteration (1 without bb) */
 } oslalm_stats;
 
 typedef struct oslalm_geom oslalm_geom;
@@ -237,8 +247,11 @@ int oslalm_fbp_noalloc(const oslalm_geom *g, const float *sino, float *x, int cl
  * oslalm_cost: *out[host] = Psi(x) = 1/2 sum_i w_i (y_i - [Ax]_i)^2 + R(x),
  *   projections accumulated and reduced in FP64; synchronizes `stream`.
  * oslalm_get_state / oslalm_set_state: the iteration state for an exact
- *   resume: g and zeta [dev, image each, FP32], *rho_l_j[host, 3 doubles] =
- *   {rho, l, j} (j = subset-iterations done).  Both synchronize `stream`. */
+ *   resume: g and zeta [dev, image each, FP32], rho_l_j[host, 4 doubles] =
+ *   {rho, l, j, alpha} (j = subset-iterations done, alpha the
+ *   Barzilai-Borwein scale).  With bb the per-subset secant history is not
+ *   part of the state: after oslalm_set_state it starts again (alpha is kept
+ *   for the next iteration).  Both synchronize `stream`. */
 int oslalm_problem_create(const oslalm_geom *g, const float *y, const float *w,
                           const oslalm_params *params, oslalm_problem **out);
 int oslalm_problem_destroy(oslalm_problem *p);

@@ -44,11 +44,17 @@ scale_factor_alpha_k), optional: the majorizer L_diag of the x-update becomes
 H_k = alpha_k L_diag, with alpha_k the weighted least-squares fit of the secant
 equation y_k ~ H_k s_k under P = L_diag^-1 and alpha <= 1:
     alpha* = s'y / s'L_diag s,  alpha = min(alpha*, 1).
-Readings: as for the restart test (Sec. III-B), the gradients are replaced by
-their subset approximations, so s = x+ - x and y = zeta+ - zeta of each
-subset-iteration, and alpha is refitted at every subset-iteration and used by
-the next x-update; alpha = 1 (the plain majorizer) at the start and whenever
-the fit has no positive curvature (s'y <= 0) or s = 0.
+Readings: k is the outer iteration (M subset-iterations), and the gradients
+are replaced by their subset approximations with the SAME subset one
+iteration apart: subset m's gradient zeta_m = M grad l_m is computed once per
+iteration, at some iterate x_m; its secant pair over the last iteration is
+s_m = x_m^(k) - x_m^(k-1), y_m = zeta_m^(k) - zeta_m^(k-1) (= M A_m'W_m A_m s_m
+for the data term, a curvature of the subset that never changes sign; the
+gradients of two different subsets would not be).  At the end of iteration k
+    alpha = min(sum_m s_m'y_m / sum_m s_m'L_diag s_m, 1)
+over the subsets with a pair, and H = alpha L_diag serves the x-updates of
+iteration k + 1.  alpha = 1 (the plain majorizer) until the first pairs exist
+and whenever the fit has no positive curvature (sum s'y <= 0) or s = 0.
 """
 from __future__ import annotations
 
@@ -251,17 +257,6 @@ def fista_momentum(n: int):
     return out
 
 
-def bb_scale(s, y, D) -> float:
-    """Barzilai-Borwein scale of the majorizer (supplement Eq.
-    scale_factor_alpha_k): argmin_{alpha <= 1} 1/2 ||y - alpha D s||^2_{D^-1},
-    i.e. min(s'y / s'Ds, 1); 1 when s'y <= 0 or s'Ds = 0 (reading)."""
-    num = float(np.sum(s * y))
-    den = float(np.sum(D * s * s))
-    if not (den > 0.0 and num > 0.0):
-        return 1.0
-    return min(num / den, 1.0)
-
-
 class OsLalm:
     """OS-LALM with n inner FISTA steps (n = 1: one projected SQS step),
     fixed rho or downward continuation, optional Barzilai-Borwein scaling of
@@ -286,6 +281,8 @@ class OsLalm:
         self.n_inner = int(n_inner)
         self.bb = bool(bb)
         self.alpha = 1.0
+        self._bb_prev = {}  # subset -> (x, zeta) of its last gradient evaluation
+        self._bb_sums = [0.0, 0.0]  # sum s'y, sum s'Ds of the current iteration
         self.history = []
 
     def init(self, x0):
@@ -296,6 +293,8 @@ class OsLalm:
         self.l = 0
         self.rho = 1.0 if self.rho_mode == "continuation" else self.rho_fixed
         self.alpha = 1.0
+        self._bb_prev = {self.order[0]: (self.x.copy(), self.zeta.copy())}
+        self._bb_sums = [0.0, 0.0]
 
     def _reg(self, x):
         if self.beta == 0.0:
@@ -351,8 +350,17 @@ class OsLalm:
             self.l = 0 if restart else self.l + 1
             self.rho = rho_l(self.l, self.rho_min)
         alpha_used = self.alpha
-        if self.bb:  # secant fit with the subset-gradient approximations
-            self.alpha = bb_scale(x_new - x, zeta_new - zeta, self.D)
+        if self.bb:  # secant pair of subset m_next over the last iteration
+            prev = self._bb_prev.get(m_next)
+            if prev is not None:
+                sk, yk = x_new - prev[0], zeta_new - prev[1]
+                self._bb_sums[0] += float(np.sum(sk * yk))
+                self._bb_sums[1] += float(np.sum(self.D * sk * sk))
+            self._bb_prev[m_next] = (x_new.copy(), zeta_new.copy())
+            if (self.j + 1) % self.M == 0:  # end of an iteration: refit H = alpha D
+                num, den = self._bb_sums
+                self.alpha = min(num / den, 1.0) if (den > 0.0 and num > 0.0) else 1.0
+                self._bb_sums = [0.0, 0.0]
         self.history.append(dict(j=self.j, rho_used=rho, xi=xi, restart=restart, l=self.l,
                                  alpha_used=alpha_used, alpha=self.alpha))
         self.x, self.g, self.zeta = x_new, g_new, zeta_new

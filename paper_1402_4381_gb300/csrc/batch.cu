@@ -95,9 +95,10 @@ __global__ void __launch_bounds__(256) batch_update_kernel(const SliceDesc *__re
         const float *xin = (step & 1) ? d.xalt : d.x;
         float *xout = (step & 1) ? d.x : d.xalt;
         const float rho = (float)d.ua.state->rho;
+        const float rho_d = (float)(d.ua.state->rho * d.ua.state->alpha);
 #define OSL_BUPD(DT, N)                                                                                          \
     update_tile<TX, TY, DT, N>(tile, ix0, iy0, tid % TX, tid / TX, tid, 256, d.geo.nx, d.geo.ny, xin, xout,     \
-                               d.ua.zeta, d.ua.g, (const DT *)d.D, d.dscale, rho, d.beta, d.inv_delta, d.curv)
+                               d.ua.zeta, d.ua.g, (const DT *)d.D, d.dscale, rho, rho_d, d.beta, d.inv_delta, d.curv)
         if (d.nbr == 8) {
             if (d.d_dtype == OSLALM_F32) OSL_BUPD(float, 8);
             else if (d.d_dtype == OSLALM_F16) OSL_BUPD(__half, 8);
@@ -324,6 +325,7 @@ int oslalm_batch_create(oslalm_problem *const *probs, int n, oslalm_batch **out)
         if (is_3d(p->g)) return fail(OSLALM_ERR_ARG, "batches hold 2D problems only (problem %d)", s);
         if (!p->initialized) return fail(OSLALM_ERR_STATE, "problem %d: call oslalm_init first", s);
         if (p->p.n_inner != 1) return fail(OSLALM_ERR_ARG, "problem %d: batches run n_inner = 1", s);
+        if (p->p.bb) return fail(OSLALM_ERR_ARG, "problem %d: batches run without Barzilai-Borwein scaling", s);
         if (p->j_host % p->p.M) return fail(OSLALM_ERR_STATE, "problem %d is not at a whole iteration", s);
     }
     oslalm_batch *b = new (std::nothrow) oslalm_batch();

@@ -234,6 +234,8 @@ struct DevState {
     int j;        // subset-iterations done
     unsigned int counter;
     int pad;
+    double alpha;  // Barzilai-Borwein scale of the majorizer (1 without it)
+    double bb_num, bb_den;  // sum s'y, sum s'Ds of the current iteration's secant pairs
 };
 
 struct UpdateArgs {  // epilogue arguments of the fused back-projection
@@ -249,6 +251,19 @@ struct UpdateArgs {  // epilogue arguments of the fused back-projection
     double rho_min;
     double rho_fixed;
     int subset;
+    // Barzilai-Borwein fit (bb != 0): subset `subset`'s gradient zeta+ is
+    // taken at x_new; its previous gradient and iterate are in bbz, bbx
+    // ([M][npix]) if bbhave[subset]; s = x_new - bbx, y = zeta+ - bbz; the
+    // sums s'y and s'Ds go next to xi in the partials buffer (3 x blocks)
+    int bb;
+    int M;
+    long npix;
+    const float *x_new;
+    float *bbx, *bbz;
+    int *bbhave;
+    const void *D;
+    int d_dtype;
+    const float *dscale;
 };
 
 void free_matrix2d(oslalm_geom *g);  // releases the device system matrix, if any

@@ -167,7 +167,7 @@ __global__ void __launch_bounds__(128) cost2d_kernel(Geo2 g, const float *__rest
 // One block of kBpThreads threads per kBpTile^2 pixel tile (bp_tile_strips);
 // then each thread finishes two pixels of the tile.
 template <int MODE>
-__device__ __forceinline__ double bp2d_epilogue(const UpdateArgs &ua, float *out, size_t p, float acc) {
+__device__ __forceinline__ void bp2d_epilogue(const UpdateArgs &ua, float *out, size_t p, float acc, IterSums &sums) {
     if (MODE == BP_STORE) {
         out[p] = acc;
     } else if (MODE == BP_ACCUM) {
@@ -184,9 +184,8 @@ __device__ __forceinline__ double bp2d_epilogue(const UpdateArgs &ua, float *out
         const float g_old = ua.g[p];
         ua.zeta[p] = acc;
         ua.g[p] = a * acc + b * g_old;
-        return (double)(g_old - acc) * (double)(acc - z_old);
+        add_iter_terms(ua, p, g_old, z_old, acc, sums);
     }
-    return 0.0;
 }
 
 template <int MODE, bool TABLE>
@@ -198,16 +197,16 @@ __global__ void __launch_bounds__(kBpThreads, TABLE ? 5 : 8) bp2d_kernel(Geo2 g,
     if (TABLE) bp_tile_table(g, r, views, nv, blockIdx.y * gridDim.x + blockIdx.x, threadIdx.x, S);
     else bp_tile_strips(g, r, views, nv, tx0, ty0, threadIdx.x, S);
     __syncthreads();
-    double xi_local = 0.0;
+    IterSums sums{0.0, 0.0, 0.0};
 #pragma unroll
     for (int k = 0; k < kBpTile * kBpTile / kBpThreads; ++k) {
         const int i = threadIdx.x + k * kBpThreads;
         const int px = i % kBpTile, py = i / kBpTile;
         const int ix = tx0 + px, iy = ty0 + py;
         if (ix < g.nx && iy < g.ny)
-            xi_local += bp2d_epilogue<MODE>(ua, out, (size_t)iy * g.nx + ix, bp_tile_total(S, px, py));
+            bp2d_epilogue<MODE>(ua, out, (size_t)iy * g.nx + ix, bp_tile_total(S, px, py), sums);
     }
-    if (MODE == BP_UPDATE) subset_iteration_epilogue(ua, xi_local);
+    if (MODE == BP_UPDATE) subset_iteration_epilogue(ua, sums);
 }
 
 // ---------------------------------------------------------------- update
@@ -221,7 +220,7 @@ __global__ void __launch_bounds__(256) update2d_kernel(int nx, int ny, const flo
     __shared__ float tile[10 * 34];
     update_tile<32, 8, DT, NBR>(tile, blockIdx.x * 32, blockIdx.y * 8, threadIdx.x, threadIdx.y,
                                 threadIdx.y * 32 + threadIdx.x, 256, nx, ny, x, xo, zeta, gs, D, dscale,
-                                (float)st->rho, beta, inv_delta, curv_mode);
+                                (float)st->rho, (float)(st->rho * st->alpha), beta, inv_delta, curv_mode);
 }
 
 template <typename DT, int NBR>
@@ -235,7 +234,7 @@ __global__ void __launch_bounds__(256) fista2d_kernel(int nx, int ny, const floa
     __shared__ float tile[10 * 34];
     fista_tile<32, 8, DT, NBR>(tile, blockIdx.x * 32, blockIdx.y * 8, threadIdx.x, threadIdx.y,
                                threadIdx.y * 32 + threadIdx.x, 256, nx, ny, v, xk, u, uo, vo, zeta, gs, D, dscale,
-                               (float)st->rho, beta, inv_delta, curv_mode, gamma);
+                               (float)st->rho, (float)(st->rho * st->alpha), beta, inv_delta, curv_mode, gamma);
 }
 
 template <int NBR>

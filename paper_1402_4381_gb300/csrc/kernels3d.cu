@@ -380,7 +380,7 @@ __global__ void __launch_bounds__(256) bp3d_kernel(Geo3 g, const float *__restri
             }
         }
     } else {
-        double xi_local = 0.0;
+        IterSums sums{0.0, 0.0, 0.0};
         if (valid) {
             const double rho = ua.state->rho;
             const float a = (float)(rho / (rho + 1.0));
@@ -394,10 +394,10 @@ __global__ void __launch_bounds__(256) bp3d_kernel(Geo3 g, const float *__restri
                 const float g_old = ua.g[p];
                 ua.zeta[p] = acc[q];
                 ua.g[p] = a * acc[q] + b * g_old;
-                xi_local += (double)(g_old - acc[q]) * (double)(acc[q] - z_old);
+                add_iter_terms(ua, p, g_old, z_old, acc[q], sums);
             }
         }
-        subset_iteration_epilogue(ua, xi_local);
+        subset_iteration_epilogue(ua, sums);
     }
 }
 
@@ -452,9 +452,9 @@ __global__ void __launch_bounds__(256) update3d_kernel(int nx, int ny, int nz, c
     stencil3d<NBR>(x, nx, ny, nz, ix, iy, iz, xj, inv_delta, curv_mode, grad, curv);
     grad *= beta;
     curv *= 2.f * beta;
-    const float rho = (float)st->rho;
+    const float rho = (float)st->rho, rho_d = (float)(st->rho * st->alpha);  // alpha: Barzilai-Borwein scale
     const float s = rho * __ldg(zeta + p) + (1.f - rho) * __ldg(gs + p);
-    const float den = rho * (load_w(D, p) * __ldg(dscale)) + curv;
+    const float den = rho_d * (load_w(D, p) * __ldg(dscale)) + curv;
     const float xn = xj - (s + grad) / den;
     xo[p] = fmaxf(xn, 0.f);
 }
@@ -476,9 +476,9 @@ __global__ void __launch_bounds__(256) fista3d_kernel(int nx, int ny, int nz, co
     stencil3d<NBR>(v, nx, ny, nz, ix, iy, iz, vj, inv_delta, curv_mode, grad, curv);
     grad *= beta;
     curv *= 2.f * beta;
-    const float rho = (float)st->rho;
+    const float rho = (float)st->rho, rho_d = (float)(st->rho * st->alpha);
     const float s = rho * __ldg(zeta + p) + (1.f - rho) * __ldg(gs + p);
-    const float rd = rho * (load_w(D, p) * __ldg(dscale));
+    const float rd = rho_d * (load_w(D, p) * __ldg(dscale));
     const float gphi = fmaf(rd, vj - __ldg(xk + p), s + grad);
     const float un = fmaxf(vj - gphi / (rd + curv), 0.f);
     uo[p] = un;

@@ -73,16 +73,63 @@ __device__ __forceinline__ double rho_of_l(int l, double rho_min) {
     return v > rho_min ? v : rho_min;
 }
 
-// Last block of a grid: reduce the per-block xi partials in a fixed order and
+// D at pixel p (dequantized) for the Barzilai-Borwein sum s'Ds.
+__device__ __forceinline__ double bb_dval(const UpdateArgs &ua, size_t p) {
+    float v;
+    if (ua.d_dtype == OSLALM_F32) v = load_w((const float *)ua.D, p);
+    else if (ua.d_dtype == OSLALM_F16) v = load_w((const __half *)ua.D, p);
+    else v = load_w((const __nv_bfloat16 *)ua.D, p);
+    return (double)v * (double)__ldg(ua.dscale);
+}
+
+// Per-pixel terms of the subset-iteration's reductions: the restart
+// indicator xi += (g - zeta+)(zeta+ - zeta) (old g, old zeta) and, with the
+// Barzilai-Borwein fit, the secant pair of this subset over the last
+// iteration (supplement Eq. scale_factor_alpha_k): s'y += s (zeta+ - zeta_m)
+// and s'Ds += D s^2, s = x_new - x_m, where (x_m, zeta_m) is where and what
+// this subset's gradient was last time; then (x_new, zeta+) replace them.
+struct IterSums {
+    double xi, sy, sds;
+};
+
+__device__ __forceinline__ void add_iter_terms(const UpdateArgs &ua, size_t p, float g_old, float z_old, float zn,
+                                               IterSums &acc) {
+    acc.xi += (double)(g_old - zn) * (double)(zn - z_old);
+    if (ua.bb) {
+        const size_t q = (size_t)ua.subset * (size_t)ua.npix + p;
+        const float xn = __ldg(ua.x_new + p);
+        if (ua.bbhave[ua.subset]) {
+            const double s = (double)xn - (double)ua.bbx[q];
+            acc.sy += s * ((double)zn - (double)ua.bbz[q]);
+            acc.sds += bb_dval(ua, p) * s * s;
+        }
+        ua.bbx[q] = xn;
+        ua.bbz[q] = zn;
+    }
+}
+
+// Last block of a grid: reduce the per-block partials in a fixed order and
 // advance the continuation state (Sec. III-B): restart (l = 0) when xi > 0,
-// else l + 1; rho = rho_l.  One thread writes the state.
+// else l + 1; rho = rho_l; with Barzilai-Borwein scaling, the secant sums
+// are added up over the iteration and at its end alpha = min(s'y / s'Ds, 1),
+// or 1 when s'y <= 0 or s'Ds = 0.  One thread writes the state.
 __device__ __forceinline__ void finish_subset_iteration(const UpdateArgs &ua, int nblocks) {
     __shared__ double red_last[32];
-    double v = 0.0;
+    double v = 0.0, vy = 0.0, vd = 0.0;
     const int nt = blockDim.x * blockDim.y * blockDim.z;
     const int tid = (threadIdx.z * blockDim.y + threadIdx.y) * blockDim.x + threadIdx.x;
-    for (int i = tid; i < nblocks; i += nt) v += __ldcg(ua.partials + i);
+    for (int i = tid; i < nblocks; i += nt) {
+        v += __ldcg(ua.partials + i);
+        if (ua.bb) {
+            vy += __ldcg(ua.partials + nblocks + i);
+            vd += __ldcg(ua.partials + 2 * nblocks + i);
+        }
+    }
     v = block_sum2d(v, red_last);
+    if (ua.bb) {
+        vy = block_sum2d(vy, red_last);
+        vd = block_sum2d(vd, red_last);
+    }
     if (tid == 0) {
         DevState *st = ua.state;
         const double xi = v;
@@ -100,6 +147,17 @@ __device__ __forceinline__ void finish_subset_iteration(const UpdateArgs &ua, in
             l = restart ? 0 : l + 1;
             rho = rho_of_l(l, ua.rho_min);
         }
+        if (ua.bb) {  // refit H = alpha D at the end of every iteration
+            st->bb_num += vy;
+            st->bb_den += vd;
+            ua.bbhave[ua.subset] = 1;
+            if ((j + 1) % ua.M == 0) {
+                const double num = st->bb_num, den = st->bb_den;
+                st->alpha = (den > 0.0 && num > 0.0) ? fmin(num / den, 1.0) : 1.0;
+                st->bb_num = 0.0;
+                st->bb_den = 0.0;
+            }
+        }
         st->xi = xi;
         st->l = l;
         st->rho = rho;
@@ -111,6 +169,7 @@ __device__ __forceinline__ void finish_subset_iteration(const UpdateArgs &ua, in
             rec.restart = restart;
             rec.subset = ua.subset;
             rec.pad = 0;
+            rec.alpha = st->alpha;
             ua.stats[j % ua.stats_cap] = rec;
         }
         st->j = j + 1;
@@ -119,17 +178,26 @@ __device__ __forceinline__ void finish_subset_iteration(const UpdateArgs &ua, in
     }
 }
 
-// Block sum of the threads' xi contributions into the partials buffer; the
-// last block to arrive finishes the subset-iteration.  Called by every thread.
-__device__ __forceinline__ void subset_iteration_epilogue(const UpdateArgs &ua, double xi_local) {
+// Block sums of the threads' terms into the partials buffer; the last block
+// to arrive finishes the subset-iteration.  Called by every thread.
+__device__ __forceinline__ void subset_iteration_epilogue(const UpdateArgs &ua, const IterSums &loc) {
     __shared__ double red[32];
     __shared__ int is_last;
-    const double bs = block_sum2d(xi_local, red);
+    const double bs = block_sum2d(loc.xi, red);
+    double by = 0.0, bd = 0.0;
+    if (ua.bb) {
+        by = block_sum2d(loc.sy, red);
+        bd = block_sum2d(loc.sds, red);
+    }
     const int nblocks = gridDim.x * gridDim.y * gridDim.z;
     const int tid = (threadIdx.z * blockDim.y + threadIdx.y) * blockDim.x + threadIdx.x;
     if (tid == 0) {
         const int bid = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
         ua.partials[bid] = bs;
+        if (ua.bb) {
+            ua.partials[nblocks + bid] = by;
+            ua.partials[2 * nblocks + bid] = bd;
+        }
         __threadfence();
         unsigned t = atomicAdd(&ua.state->counter, 1u);
         is_last = (t == (unsigned)(nblocks - 1));

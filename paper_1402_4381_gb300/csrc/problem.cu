@@ -97,8 +97,11 @@ __global__ void fill_kernel(float *__restrict__ a, size_t n, float v) {
     if (i < n) a[i] = v;
 }
 
-__global__ void set_state_kernel(DevState *st, double rho, int l, int j) {
+__global__ void set_state_kernel(DevState *st, double rho, int l, int j, double alpha) {
     st->rho = rho;
+    st->alpha = alpha;
+    st->bb_num = 0.0;
+    st->bb_den = 0.0;
     st->xi = 0.0;
     st->l = l;
     st->j = j;
@@ -181,6 +184,15 @@ UpdateArgs update_args(oslalm_problem *p, int subset) {
     a.rho_min = p->p.rho_min;
     a.rho_fixed = p->p.rho_fixed;
     a.subset = subset;
+    a.bb = p->p.bb;
+    a.M = p->p.M;
+    a.npix = p->npix;
+    a.bbx = p->d_bbx;
+    a.bbz = p->d_bbz;
+    a.bbhave = p->d_bbhave;
+    a.D = p->d_D;
+    a.d_dtype = p->p.d_dtype;
+    a.dscale = p->d_dscale;
     return a;
 }
 
@@ -265,8 +277,11 @@ int update_step(oslalm_problem *p, const float *x_in, float *x_out, cudaStream_t
     return OSLALM_OK;
 }
 
-int bp_update(oslalm_problem *p, int next, cudaStream_t st) {
+// back-projection with the split-gradient update; x_new is the iterate at
+// which subset `next`'s gradient is taken (Barzilai-Borwein secant pairs)
+int bp_update(oslalm_problem *p, int next, const float *x_new, cudaStream_t st) {
     UpdateArgs ua = update_args(p, next);
+    ua.x_new = x_new;
     return launch_bp_any(p->g, p->d_r, nullptr, p->d_views + p->off[next], p->cnt[next], BP_UPDATE, &ua, st);
 }
 
@@ -274,7 +289,7 @@ int bp_update(oslalm_problem *p, int next, cudaStream_t st) {
 int subset_iteration(oslalm_problem *p, const float *x_in, float *x_out, int next, cudaStream_t st) {
     if (int rc = update_step(p, x_in, x_out, st)) return rc;
     if (int rc = fp_subset(p, x_out, next, FP_RESID, (float)p->p.M, st)) return rc;
-    return bp_update(p, next, st);
+    return bp_update(p, next, x_out, st);
 }
 
 // `iters` whole iterations starting at subset-iteration j0 (a multiple of M)
@@ -346,6 +361,7 @@ void free_problem(oslalm_problem *p) {
     cudaFree(p->d_r); cudaFree(p->d_tmp); cudaFree(p->d_state); cudaFree(p->d_partials); cudaFree(p->d_stats);
     cudaFree(p->d_replay);
     cudaFree(p->d_fu[0]); cudaFree(p->d_fu[1]); cudaFree(p->d_fv[0]); cudaFree(p->d_fv[1]);
+    cudaFree(p->d_bbx); cudaFree(p->d_bbz); cudaFree(p->d_bbhave);
     delete p;
 }
 
@@ -389,6 +405,7 @@ int oslalm_problem_create(const oslalm_geom *g, const float *y, const float *w, 
     if (pp.rho_mode != OSLALM_RHO_FIXED && !(pp.rho_min > 0 && pp.rho_min <= 1)) return fail(OSLALM_ERR_ARG, "need 0 < rho_min <= 1");
     if (pp.w_dtype < 0 || pp.w_dtype > 2 || pp.d_dtype < 0 || pp.d_dtype > 2) return fail(OSLALM_ERR_ARG, "bad dtype");
     if (pp.curvature != OSLALM_CURV_HUBER && pp.curvature != OSLALM_CURV_MAX) return fail(OSLALM_ERR_ARG, "bad curvature");
+    if (pp.bb != 0 && pp.bb != 1) return fail(OSLALM_ERR_ARG, "bb must be 0 or 1");
     int p_n_partials_tmp = 0;
     oslalm_problem *p = new (std::nothrow) oslalm_problem();
     if (!p) return fail(OSLALM_ERR_ALLOC, "host allocation failed");
@@ -422,6 +439,7 @@ int oslalm_problem_create(const oslalm_geom *g, const float *y, const float *w, 
         const oslalm_geom_desc &dd = g->d;
         long reg_blocks = (long)((dd.nx + 31) / 32) * ((dd.ny + 7) / 8) * dd.nz;
         long np = (long)nblk(nsino, 128) + pp.M + std::max<long>(reg_blocks, bp_blocks_any(g)) + 64;
+        np = std::max<long>(np, 3L * bp_blocks_any(g) + 64);  // xi, s'y, s'Ds per back-projection block
         if (np > (1L << 30)) {
             delete p;
             return fail(OSLALM_ERR_RANGE, "problem too large");
@@ -451,6 +469,11 @@ int oslalm_problem_create(const oslalm_geom *g, const float *y, const float *w, 
             OSL_ALLOC(p->d_fu[k], sizeof(float) * p->npix);
             OSL_ALLOC(p->d_fv[k], sizeof(float) * p->npix);
         }
+    }
+    if (pp.bb) {
+        OSL_ALLOC(p->d_bbx, sizeof(float) * p->npix * pp.M);
+        OSL_ALLOC(p->d_bbz, sizeof(float) * p->npix * pp.M);
+        OSL_ALLOC(p->d_bbhave, sizeof(int) * pp.M);
     }
 #undef OSL_ALLOC
     if (e != cudaSuccess) {
@@ -498,8 +521,17 @@ int oslalm_init(oslalm_problem *p, const float *x, void *stream) {
     if (int rc = launch_bp_any(p->g, p->d_r, nullptr, p->d_views + p->off[m0], p->cnt[m0], BP_INIT, &ua, st))
         return rc;
     const double rho0 = p->p.rho_mode == OSLALM_RHO_FIXED ? p->p.rho_fixed : 1.0;
-    set_state_kernel<<<1, 1, 0, st>>>(p->d_state, rho0, 0, 0);
+    set_state_kernel<<<1, 1, 0, st>>>(p->d_state, rho0, 0, 0, 1.0);
     OSL_LAUNCH_CHECK("set_state");
+    if (p->p.bb) {  // the first gradient (subset sigma(0) at x0) opens its secant history
+        const size_t nb = sizeof(float) * p->npix;
+        OSL_CUDA_TRY(cudaMemsetAsync(p->d_bbhave, 0, sizeof(int) * p->p.M, st));
+        OSL_CUDA_TRY(cudaMemcpyAsync(p->d_bbx + (size_t)m0 * p->npix, x, nb, cudaMemcpyDeviceToDevice, st));
+        OSL_CUDA_TRY(cudaMemcpyAsync(p->d_bbz + (size_t)m0 * p->npix, p->d_zeta, nb, cudaMemcpyDeviceToDevice, st));
+        const int one = 1;
+        OSL_CUDA_TRY(cudaMemcpyAsync(p->d_bbhave + m0, &one, sizeof(int), cudaMemcpyHostToDevice, st));
+        OSL_CUDA_TRY(cudaStreamSynchronize(st));  // `one` lives on this stack frame
+    }
     p->j_host = 0;
     p->initialized = true;
     return OSLALM_OK;
@@ -561,7 +593,7 @@ int oslalm_profile_iterate(oslalm_problem *p, float *x, int n_iter, double *ms_o
             if (!rc) rc = fp_subset(p, nxt, next, FP_RESID, (float)M, st);
             cudaEventRecord(ev[6 * k + 3], st);
             cudaEventRecord(ev[6 * k + 4], st);
-            if (!rc) rc = bp_update(p, next, st);
+            if (!rc) rc = bp_update(p, next, nxt, st);
             cudaEventRecord(ev[6 * k + 5], st);
             std::swap(cur, nxt);
         }
@@ -661,6 +693,7 @@ int oslalm_get_state(oslalm_problem *p, float *g, float *zeta, double *rho_l_j, 
         rho_l_j[0] = h.rho;
         rho_l_j[1] = h.l;
         rho_l_j[2] = h.j;
+        rho_l_j[3] = h.alpha;
     }
     return OSLALM_OK;
 }
@@ -675,8 +708,9 @@ int oslalm_set_state(oslalm_problem *p, const float *g, const float *zeta, const
     cudaStream_t st = (cudaStream_t)stream;
     OSL_CUDA_TRY(cudaMemcpyAsync(p->d_g, g, p->npix * sizeof(float), cudaMemcpyDeviceToDevice, st));
     OSL_CUDA_TRY(cudaMemcpyAsync(p->d_zeta, zeta, p->npix * sizeof(float), cudaMemcpyDeviceToDevice, st));
-    set_state_kernel<<<1, 1, 0, st>>>(p->d_state, rho_l_j[0], (int)rho_l_j[1], (int)j);
+    set_state_kernel<<<1, 1, 0, st>>>(p->d_state, rho_l_j[0], (int)rho_l_j[1], (int)j, rho_l_j[3]);
     OSL_LAUNCH_CHECK("set_state");
+    if (p->p.bb) OSL_CUDA_TRY(cudaMemsetAsync(p->d_bbhave, 0, sizeof(int) * p->p.M, st));  // secant history restarts
     OSL_CUDA_TRY(cudaStreamSynchronize(st));
     p->j_host = j;
     return OSLALM_OK;

@@ -22,6 +22,8 @@ struct oslalm_problem {
     float *d_g = nullptr, *d_zeta = nullptr, *d_xalt = nullptr;
     float *d_fu[2] = {nullptr, nullptr}, *d_fv[2] = {nullptr, nullptr};  // inner FISTA iterates (n_inner > 1)
     std::vector<float> fista_gamma;                                     // momentum weights of the inner steps
+    float *d_bbx = nullptr, *d_bbz = nullptr;  // Barzilai-Borwein: per subset, last gradient's iterate and value [M][npix]
+    int *d_bbhave = nullptr;                   // [M]: 1 once subset m has a stored pair
     float *d_r = nullptr;    // residual of one subset
     float *d_tmp = nullptr;  // full-sinogram scratch (set_data staging)
     oslalm::DevState *d_state = nullptr;

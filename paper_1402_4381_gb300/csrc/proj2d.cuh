@@ -335,7 +335,8 @@ __device__ __forceinline__ void load_tile_halo(float *tile, int ix0, int iy0, in
 }
 
 // The n = 1 inner step on one TX x TY tile of pixels (Sec. IV-A):
-// s = rho zeta + (1-rho) g; x+ = max(0, x - (s + grad R(x)) / (rho D + D_R(x))),
+// s = rho zeta + (1-rho) g; x+ = max(0, x - (s + grad R(x)) / (rho_d D + D_R(x))),
+// rho_d = rho alpha (alpha = 1 without Barzilai-Borwein scaling),
 // with the 4/8-neighbour hyperbola gradient and Huber curvature read from a
 // shared-memory copy of the tile and its one-pixel halo.  (tx, ty): this
 // thread's pixel in the tile; tid/nthreads: its rank for the cooperative load.
@@ -345,7 +346,7 @@ __device__ __forceinline__ void update_tile(float *tile, int ix0, int iy0, int t
                                             int nx, int ny, const float *__restrict__ x, float *__restrict__ xo,
                                             const float *__restrict__ zeta, const float *__restrict__ gs,
                                             const DT *__restrict__ D, const float *__restrict__ dscale, float rho,
-                                            float beta, float inv_delta, int curv_mode) {
+                                            float rho_d, float beta, float inv_delta, int curv_mode) {
     load_tile_halo<TX, TY>(tile, ix0, iy0, tid, nthreads, nx, ny, x);
     const int ix = ix0 + tx, iy = iy0 + ty;
     if (ix < nx && iy < ny) {
@@ -356,7 +357,7 @@ __device__ __forceinline__ void update_tile(float *tile, int ix0, int iy0, int t
         curv *= 2.f * beta;
         const size_t p = (size_t)iy * nx + ix;
         const float s = rho * __ldg(zeta + p) + (1.f - rho) * __ldg(gs + p);
-        const float den = rho * (load_w(D, p) * __ldg(dscale)) + curv;
+        const float den = rho_d * (load_w(D, p) * __ldg(dscale)) + curv;
         const float xn = xj - (s + grad) / den;
         xo[p] = fmaxf(xn, 0.f);
     }
@@ -373,7 +374,7 @@ __device__ __forceinline__ void fista_tile(float *tile, int ix0, int iy0, int tx
                                            const float *__restrict__ u, float *__restrict__ uo, float *__restrict__ vo,
                                            const float *__restrict__ zeta, const float *__restrict__ gs,
                                            const DT *__restrict__ D, const float *__restrict__ dscale, float rho,
-                                           float beta, float inv_delta, int curv_mode, float gamma) {
+                                           float rho_d, float beta, float inv_delta, int curv_mode, float gamma) {
     load_tile_halo<TX, TY>(tile, ix0, iy0, tid, nthreads, nx, ny, v);
     const int ix = ix0 + tx, iy = iy0 + ty;
     if (ix < nx && iy < ny) {
@@ -384,7 +385,7 @@ __device__ __forceinline__ void fista_tile(float *tile, int ix0, int iy0, int tx
         curv *= 2.f * beta;
         const size_t p = (size_t)iy * nx + ix;
         const float s = rho * __ldg(zeta + p) + (1.f - rho) * __ldg(gs + p);
-        const float rd = rho * (load_w(D, p) * __ldg(dscale));
+        const float rd = rho_d * (load_w(D, p) * __ldg(dscale));
         const float gphi = fmaf(rd, vj - __ldg(xk + p), s + grad);
         const float un = fmaxf(vj - gphi / (rd + curv), 0.f);
         uo[p] = un;

@@ -42,12 +42,12 @@ class Params(ctypes.Structure):
     _fields_ = [("beta", ctypes.c_double), ("delta", ctypes.c_double), ("nbr", ctypes.c_int), ("M", ctypes.c_int),
                 ("rho_min", ctypes.c_double), ("n_inner", ctypes.c_int), ("rho_mode", ctypes.c_int),
                 ("rho_fixed", ctypes.c_double), ("curvature", ctypes.c_int), ("w_dtype", ctypes.c_int),
-                ("d_dtype", ctypes.c_int), ("use_graph", ctypes.c_int)]
+                ("d_dtype", ctypes.c_int), ("use_graph", ctypes.c_int), ("bb", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
     _fields_ = [("xi", ctypes.c_double), ("rho_used", ctypes.c_double), ("l", ctypes.c_int),
-                ("restart", ctypes.c_int), ("subset", ctypes.c_int), ("pad", ctypes.c_int)]
+                ("restart", ctypes.c_int), ("subset", ctypes.c_int), ("pad", ctypes.c_int), ("alpha", ctypes.c_double)]
 
 
 _lib = None
@@ -270,7 +270,8 @@ class Problem:
     """PWLS problem + OS-LALM state (oslalm_problem)."""
 
     def __init__(self, geom: Geometry, y, w, *, beta, delta, nbr, M, rho_min=1e-3, rho_mode="continuation",
-                 rho_fixed=1.0, curvature="huber", w_dtype="f32", d_dtype="f32", use_graph=True, n_inner=1):
+                 rho_fixed=1.0, curvature="huber", w_dtype="f32", d_dtype="f32", use_graph=True, n_inner=1,
+                 bb=False):
         self.geom = geom
         shape = geom.sino_shape()
         _dev_f32(y, shape, "y")
@@ -282,6 +283,7 @@ class Problem:
         p.curvature = CURV_HUBER if curvature == "huber" else CURV_MAX
         p.w_dtype, p.d_dtype = _DTYPES[w_dtype], _DTYPES[d_dtype]
         p.use_graph = int(bool(use_graph))
+        p.bb = int(bool(bb))
         self.params = p
         self.M = int(M)
         self._h = _VP()
@@ -305,7 +307,8 @@ class Problem:
             buf = (Stats * (n_iter * self.M))()
         _check(lib().oslalm_iterate(self._h, _ptr(x), int(n_iter), buf, _stream(stream)), "iterate")
         if stats:
-            return [dict(xi=s.xi, rho_used=s.rho_used, l=s.l, restart=bool(s.restart), subset=s.subset) for s in buf]
+            return [dict(xi=s.xi, rho_used=s.rho_used, l=s.l, restart=bool(s.restart), subset=s.subset, alpha=s.alpha)
+                    for s in buf]
         return None
 
     def profile_iterate(self, x, n_iter=1, stream=None):
@@ -333,12 +336,12 @@ class Problem:
         shape = self.geom.image_shape
         g = torch.empty(shape, dtype=torch.float32, device="cuda")
         z = torch.empty(shape, dtype=torch.float32, device="cuda")
-        s = (ctypes.c_double * 3)()
+        s = (ctypes.c_double * 4)()
         _check(lib().oslalm_get_state(self._h, _ptr(g), _ptr(z), s, _stream(stream)), "get_state")
-        return dict(g=g, zeta=z, rho=s[0], l=int(s[1]), j=int(s[2]))
+        return dict(g=g, zeta=z, rho=s[0], l=int(s[1]), j=int(s[2]), alpha=s[3])
 
     def set_state(self, st, stream=None):
-        s = (ctypes.c_double * 3)(st["rho"], st["l"], st["j"])
+        s = (ctypes.c_double * 4)(st["rho"], st["l"], st["j"], st.get("alpha", 1.0))
         _check(lib().oslalm_set_state(self._h, _ptr(st["g"]), _ptr(st["zeta"]), s, _stream(stream)), "set_state")
 
     def denominator(self, stream=None):

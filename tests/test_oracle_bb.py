@@ -4,6 +4,10 @@ secant_eq and scale_factor_alpha_k) against what the mathematics fixes:
 * on a quadratic data term with one subset, the gradient difference is
   A'WA s exactly, so the oracle's fitted scale must equal s'A'WAs / s'Ds
   computed from the dense matrix (and lie in (0, 1): D majorizes A'WA);
+* with M subsets, each subset's gradient difference over one iteration is
+  M A_m'W_m A_m s_m exactly, so the scale fitted at the end of an iteration
+  must equal sum_m M s_m'A_m'W_m A_m s_m / sum_m s_m'D s_m from the dense
+  per-subset matrices and the iterates at which the gradients were taken;
 * with rho = 1, no regularizer and no constraint, OS-LALM with BB scaling is
   the textbook diagonally preconditioned Barzilai-Borwein gradient method;
 * the constraint alpha <= 1 caps the fit when D does not majorize;
@@ -125,3 +129,33 @@ def test_bb_changes_the_path_not_the_minimiser():
     free = x > 1e-9
     assert np.max(np.abs(g[free])) < 1e-7 * np.abs(data.At_m(data.w[0] * data.y[0], 0)).max()
     assert any(h["alpha_used"] < 1.0 for h in out[1].history)
+
+
+def test_bb_scale_with_subsets_is_the_per_subset_secant_fit():
+    A, w, y = _quadratic(5, m=45, n=12)
+    n = A.shape[1]
+    M = 3
+    rows = [np.arange(m, A.shape[0], M) for m in range(M)]
+    img = lambda v: v.reshape(1, 1, -1)  # noqa: E731
+    data = O.SubsetData(lambda x, m: A[rows[m]] @ x.ravel(), lambda r, m: img(A[rows[m]].T @ r),
+                        [y[r] for r in rows], [w[r] for r in rows], M)
+    D = A.T @ (w * (A @ np.ones(n)))
+    Hm = [M * A[r].T @ (w[r][:, None] * A[r]) for r in rows]
+    alg = O.OsLalm(data, img(D), beta=0.0, delta=1.0, nbr=4, rho_mode="fixed", rho_fixed=0.5, nonneg=False,
+                   bb=True)
+    alg.init(img(np.full(n, 0.3)))
+    at = {alg.order[0]: [alg.x.ravel().copy()]}  # iterates where each subset's gradient was taken
+    for k in range(4):
+        num = den = 0.0
+        for q in range(M):
+            alg.step()
+            m = alg.order[(alg.j) % M]
+            x = alg.x.ravel().copy()
+            if m in at:
+                sm = x - at[m][-1]
+                num += float(sm @ Hm[m] @ sm)
+                den += float(sm @ (D * sm))
+            at.setdefault(m, []).append(x)
+        assert den > 0.0
+        assert alg.history[-1]["alpha"] == pytest.approx(min(num / den, 1.0), rel=1e-10)
+        assert alg.history[-1]["alpha"] < 1.0
