@@ -296,9 +296,13 @@ __global__ void __launch_bounds__(256) bp3d_kernel(Geo3 g, const float *__restri
     const int iy = blockIdx.y * 8 + threadIdx.y;
     const int kz0 = blockIdx.z * KZ;
     const bool valid = ix < g.nx && iy < g.ny;
-    float acc[KZ];
+    // the column's KZ accumulators in shared memory, word q * 256 + thread
+    // (bank = thread mod 32: conflict free), so that a detector row adds to
+    // only the one or two voxels it crosses
+    __shared__ float accs[KZ * 256];
+    float *acc = accs + threadIdx.y * 32 + threadIdx.x;
 #pragma unroll
-    for (int q = 0; q < KZ; ++q) acc[q] = 0.f;
+    for (int q = 0; q < KZ; ++q) acc[q * 256] = 0.f;
     if (valid) {
         const float px = g.xlo + ((float)ix + 0.5f) * g.dx;
         const float py = g.ylo + ((float)iy + 0.5f) * g.dy;
@@ -350,14 +354,11 @@ __global__ void __launch_bounds__(256) bp3d_kernel(Geo3 g, const float *__restri
                     if (khi < kz0 || klo >= kz0 + KZ) continue;
                     const bool zinc = z.inc;
                     const float val = __ldg(rv + (size_t)t * g.ns + c);
-#pragma unroll
-                    for (int q = 0; q < KZ; ++q) {
-                        const int kz = kz0 + q;
-                        if (kz >= klo && kz <= khi) {
-                            float zlo_, zhi_;
-                            dcell_frac(sz_, zinc, (float)(kz - sz_.base), zlo_, zhi_);
-                            acc[q] = fmaf(pair_len(blo, bhi, zlo_, zhi_, z.L), val, acc[q]);
-                        }
+                    const int q1 = min(khi, kz0 + KZ - 1) - kz0;
+                    for (int q = max(klo, kz0) - kz0; q <= q1; ++q) {
+                        float zlo_, zhi_;
+                        dcell_frac(sz_, zinc, (float)(kz0 + q - sz_.base), zlo_, zhi_);
+                        acc[q * 256] = fmaf(pair_len(blo, bhi, zlo_, zhi_, z.L), val, acc[q * 256]);
                     }
                 }
             }
@@ -372,11 +373,11 @@ __global__ void __launch_bounds__(256) bp3d_kernel(Geo3 g, const float *__restri
             const int kz = kz0 + q;
             if (kz >= g.nz) break;
             const size_t p = (size_t)kz * sz + p0;
-            if (MODE == BP_STORE) out[p] = acc[q];
-            else if (MODE == BP_ACCUM) out[p] += acc[q];
+            if (MODE == BP_STORE) out[p] = acc[q * 256];
+            else if (MODE == BP_ACCUM) out[p] += acc[q * 256];
             else {
-                ua.zeta[p] = acc[q];
-                ua.g[p] = acc[q];
+                ua.zeta[p] = acc[q * 256];
+                ua.g[p] = acc[q * 256];
             }
         }
     } else {
@@ -392,9 +393,9 @@ __global__ void __launch_bounds__(256) bp3d_kernel(Geo3 g, const float *__restri
                 const size_t p = (size_t)kz * sz + p0;
                 const float z_old = ua.zeta[p];
                 const float g_old = ua.g[p];
-                ua.zeta[p] = acc[q];
-                ua.g[p] = a * acc[q] + b * g_old;
-                add_iter_terms(ua, p, g_old, z_old, acc[q], sums);
+                ua.zeta[p] = acc[q * 256];
+                ua.g[p] = a * acc[q * 256] + b * g_old;
+                add_iter_terms(ua, p, g_old, z_old, acc[q * 256], sums);
             }
         }
         subset_iteration_epilogue(ua, sums);
