@@ -47,10 +47,11 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-time-to-hu", action="store_true")
-    ap.add_argument("--workload", default="fan", choices=["fan", "fan256", "cone", "parallel", "batch"],
+    ap.add_argument("--workload", default="fan", choices=["fan", "fan256", "cone", "helical", "parallel", "batch"],
                     help="fan: the 512^2 fan-beam scan (default, the headline); fan256: the same scan family at "
                          "256^2, 492 views, M = 12; cone / parallel: the 512x512x128 cone-beam and 128^2 "
-                         "parallel-beam scans; batch: 64 fan-beam slices of mixed sizes advanced together")
+                         "parallel-beam scans; helical: 512x512x64, 2 turns of 984 views at pitch 0.5, M = 36; "
+                         "batch: 64 fan-beam slices of mixed sizes advanced together")
     ap.add_argument("--slices", type=int, default=64)
     ap.add_argument("--matrix", action="store_true",
                     help="2D: stream the system matrix held in device memory (oslalm_geom_build_matrix) instead "
@@ -156,6 +157,10 @@ def roi_mask(geom):
     m2 = (r <= R)[None]
     if geom.kind != 2:
         return m2
+    if geom.pitch != 0.0:  # helix: the heights between the first and last source positions
+        zs = geom.source_z()
+        iz = (np.arange(geom.nz) - (geom.nz - 1) / 2.0) * geom.dz
+        return m2 & ((iz >= zs.min()) & (iz <= zs.max()))[:, None, None]
     iz = (np.arange(geom.nz) - (geom.nz - 1) / 2.0) * geom.dz
     mag = geom.dsd / np.maximum(geom.dso - r, 1e-9)
     return m2 & (np.abs(iz)[:, None, None] * mag[None] <= geom.nt * geom.dt / 2.0)
@@ -195,7 +200,8 @@ def run_reference(args):
     if rank != 0:
         return 0
     from paper_1402_4381_gb300 import workloads as W
-    wl = {"fan": W.c1_fan, "fan256": W.c1_fan_256, "cone": W.c2_cone, "parallel": W.c0_parallel}[args.workload]()
+    wl = {"fan": W.c1_fan, "fan256": W.c1_fan_256, "cone": W.c2_cone, "helical": W.c2_helical,
+          "parallel": W.c0_parallel}[args.workload]()
     scan = wl.make_scan()
     from oracle import fbp as ofbp
     x0 = np.maximum(ofbp.fbp(wl.geom, scan["y"].astype(np.float64)), 0.0)
@@ -228,7 +234,8 @@ def run_ours(args):
         torch.cuda.set_device(0)
     from paper_1402_4381_gb300 import oslalm, workloads as W
 
-    wl = {"fan": W.c1_fan, "fan256": W.c1_fan_256, "cone": W.c2_cone, "parallel": W.c0_parallel}[args.workload]()
+    wl = {"fan": W.c1_fan, "fan256": W.c1_fan_256, "cone": W.c2_cone, "helical": W.c2_helical,
+          "parallel": W.c0_parallel}[args.workload]()
     if world > 1:  # independent replicas: a different noise realisation per rank
         wl.noise_seed += 1000 * rank
     g = wl.geom
@@ -248,7 +255,10 @@ def run_ours(args):
     # initial image: FBP of the log sinogram, clipped to x >= 0 (set-up)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
-    x0 = geom.fbp(y, clip=True)
+    if g.pitch != 0.0:  # no FDK for a helix: a water cylinder over the field of view
+        x0 = torch.as_tensor(np.where(mask_np, 0.0192, 0.0).astype(np.float32), device=dev)
+    else:
+        x0 = geom.fbp(y, clip=True)
     e1.record()
     e1.synchronize()
     fbp_ms = e0.elapsed_time(e1)
@@ -358,7 +368,8 @@ def run_ours(args):
         ops = 3.0 * inter  # FP32 ops per (ray, pixel) pair: crossing, length, multiply-accumulate
         peak_ops = 152 * 128 * sm_mhz * 1e6
         achieved = ops / (per[dom] / 1000.0)
-        roof = {"kernel": {"forward": "fp2d_kernel", "backproject": "bp2d_kernel"}[dom], "bound": "alu",
+        dim = "3d" if g.kind == 2 else "2d"
+        roof = {"kernel": {"forward": f"fp{dim}_kernel", "backproject": f"bp{dim}_kernel"}[dom], "bound": "alu",
                 "achieved": achieved / 1e12, "peak": peak_ops / 1e12, "unit": "TFLOP/s",
                 "frac": achieved / peak_ops,
                 "traffic": NCU_DRAM_BYTES_FAN.get({"forward": "fp2d_kernel", "backproject": "bp2d_kernel"}[dom])

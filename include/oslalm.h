@@ -88,6 +88,10 @@ typedef struct oslalm_geom_desc {
     double ds, dt;                    /* channel / row pitch (mm at the detector) */
     double offset_s, offset_t;        /* detector offsets in channels / rows */
     double dso, dsd;                  /* source-isocentre, source-detector (mm) */
+    double pitch;                     /* cone beam: 0 = circular orbit; > 0 = helix whose
+                                         source and detector rise by pitch * nt * dt (mm)
+                                         per turn, centred on the scanned angle range:
+                                         z_v = pitch nt dt (phi_v - phi_mid) / (2 pi) */
 } oslalm_geom_desc;
 
 typedef struct oslalm_params {
@@ -182,6 +186,14 @@ int oslalm_ray_table(const oslalm_geom_desc *desc, int view, float *f0, float *k
  * views[host, capacity ceil(nviews/M)]: views of subset m (v = m, m+M, ...);
  * *n receives their count.  Errors: ARG. */
 int oslalm_subset_order(int M, int *order);
+
+/* Largest number of subsets that still gives every voxel of the central
+ * transaxial region s views per subset (Sec. IV-B): *m_max = nviews / s on a
+ * circular orbit (Eq. max_M_axial; the paper uses s = 40), and
+ * (views per turn) dso / (pitch s dsd) on a helix (Eq. max_M_helical;
+ * s = 24), views per turn = nviews 2 pi / angle_span.  A guideline (not
+ * enforced by oslalm_problem_create).  Host only.  Errors: ARG. */
+int oslalm_max_subsets(const oslalm_geom_desc *desc, double s, double *m_max);
 int oslalm_subset_views(const oslalm_geom *g, int M, int m, int *views, int *n);
 
 /* ---- projector pair (A_m and its exact transpose) -------------------------

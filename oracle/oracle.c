@@ -20,8 +20,12 @@
  *   parallel: line through s_c e along u, s_c=(c-(ns-1)/2+offset_s) ds;
  *   fan/arc : source -dso u, channel angle g_c = s_c/dsd, the ray ends on the
  *             arc of radius dsd around the source;
- *   cone/flat: source (-dso u, 0), cell centre (dsd-dso) u + s_c e + t_t z,
- *             t_t=(t-(nt-1)/2+offset_t) dt;
+ *   cone/flat: source (-dso u, z_v), cell centre (dsd-dso) u + s_c e + (z_v+t_t) z,
+ *             t_t=(t-(nt-1)/2+offset_t) dt; z_v = 0 on a circular orbit; on a
+ *             helix (pitch > 0) source and detector rise by pitch nt dt per
+ *             turn, z_v = pitch nt dt (phi_v - phi_mid)/(2 pi) with phi_mid the
+ *             middle of the scanned angle range (a central voxel is then seen
+ *             for dso/(pitch dsd) turns, as Sec. IV-B counts);
  *   pixels are half-open boxes [lo, hi): a ray lying exactly on the plane
  *   between two pixels belongs to the upper one (the midpoint rule below
  *   does this; an axis-parallel ray is inside when lo <= p < hi);
@@ -46,6 +50,7 @@ typedef struct {
     double ds, dt;
     double offset_s, offset_t;
     double dso, dsd;
+    double pitch;
 } og_geom;
 
 /* (cos(pi t), sin(pi t)) with exact quarter-turn reduction */
@@ -86,8 +91,13 @@ static void ray_segment(const og_geom *g, int view, int t, int c, double P0[3], 
     } else {
         double tt = ((double)t - (g->nt - 1) / 2.0 + g->offset_t) * g->dt;
         double dd = g->dsd - g->dso;
-        P0[0] = -g->dso * ux; P0[1] = -g->dso * uy; P0[2] = 0.0;
-        P1[0] = dd * ux + s * ex; P1[1] = dd * uy + s * ey; P1[2] = tt;
+        double zv = 0.0;
+        if (g->pitch != 0.0) {
+            double dphi = (double)view * (g->angle_span / (double)g->nviews) - 0.5 * g->angle_span;
+            zv = g->pitch * g->nt * g->dt * dphi / (2.0 * M_PI);
+        }
+        P0[0] = -g->dso * ux; P0[1] = -g->dso * uy; P0[2] = zv;
+        P1[0] = dd * ux + s * ex; P1[1] = dd * uy + s * ey; P1[2] = zv + tt;
     }
 }
 

@@ -386,7 +386,8 @@ HU = 0.0192 / 1000.0
 def roi_mask(geom):
     """Pixels inside the scanner's field of view (reading of "region of
     interest"); for the cone beam also voxels that project inside the
-    detector rows from every view."""
+    detector rows from every view (circular orbit), or lie between the first
+    and last source heights (helix)."""
     ix = (np.arange(geom.nx) - (geom.nx - 1) / 2.0) * geom.dx + geom.offset_x
     iy = (np.arange(geom.ny) - (geom.ny - 1) / 2.0) * geom.dy + geom.offset_y
     Y, X = np.meshgrid(iy, ix, indexing="ij")
@@ -399,6 +400,9 @@ def roi_mask(geom):
     if geom.kind != 2:
         return m2[None]
     iz = (np.arange(geom.nz) - (geom.nz - 1) / 2.0) * geom.dz + geom.offset_z
+    if getattr(geom, "pitch", 0.0) != 0.0:  # helix (reading): the cylinder between the first and last source heights
+        zs = geom.source_z()
+        return m2[None] & ((iz >= zs.min()) & (iz <= zs.max()))[:, None, None]
     tmax = geom.nt * geom.dt / 2.0
     mag = geom.dsd / np.maximum(geom.dso - r, 1e-9)
     return m2[None] & (np.abs(iz)[:, None, None] * mag[None] <= tmax)

@@ -20,7 +20,7 @@ class OgGeom(ctypes.Structure):
                 ("nviews", ctypes.c_int), ("angle_start", ctypes.c_double), ("angle_span", ctypes.c_double),
                 ("ns", ctypes.c_int), ("nt", ctypes.c_int), ("ds", ctypes.c_double), ("dt", ctypes.c_double),
                 ("offset_s", ctypes.c_double), ("offset_t", ctypes.c_double),
-                ("dso", ctypes.c_double), ("dsd", ctypes.c_double)]
+                ("dso", ctypes.c_double), ("dsd", ctypes.c_double), ("pitch", ctypes.c_double)]
 
 
 def lib():

@@ -139,6 +139,7 @@ extern "C" int oslalm_fbp(const oslalm_geom *gm, const float *sino, float *x, in
     const oslalm_geom_desc &d = gm->d;
     if (d.kind != OSLALM_PAR2D && fabs(fabs(d.angle_span) - 2.0 * M_PI) > 1e-9)
         return fail(OSLALM_ERR_ARG, "fan/cone FBP needs a full 360-degree scan");
+    if (d.pitch != 0.0) return fail(OSLALM_ERR_ARG, "FDK needs a circular orbit (pitch 0)");
     if (d.ns > 8192) return fail(OSLALM_ERR_RANGE, "FBP supports at most 8192 channels");
     cudaStream_t st = (cudaStream_t)stream;
     FbpGeo g;
@@ -219,6 +220,7 @@ extern "C" int oslalm_fbp_noalloc(const oslalm_geom *gm, const float *sino, floa
     const oslalm_geom_desc &d = gm->d;
     if (d.kind != OSLALM_PAR2D && fabs(fabs(d.angle_span) - 2.0 * M_PI) > 1e-9)
         return fail(OSLALM_ERR_ARG, "fan/cone FBP needs a full 360-degree scan");
+    if (d.pitch != 0.0) return fail(OSLALM_ERR_ARG, "FDK needs a circular orbit (pitch 0)");
     if (d.ns > 8192) return fail(OSLALM_ERR_RANGE, "FBP supports at most 8192 channels");
     const size_t nq = (size_t)d.nviews * d.nt * d.ns;
     if (nq > kFbpStaticFloats)

@@ -171,8 +171,14 @@ static void ray3_table_view(const oslalm_geom_desc &d, int v, Ray3 *out) {
         r.kw = kw;
         r.sw = sw;
         r.w1l = (float)(W1 - ldexp((double)kw, -sw));
-        // offset of the bottom face: zb = z/dz + nz/2 - offset_z/dz
-        double oz = 0.5 * d.nz - d.offset_z / d.dz;
+        // offset of the bottom face: zb = (z - z_v)/dz + nz/2 - offset_z/dz + z_v/dz,
+        // z_v the source height of this view (helix; 0 on a circular orbit)
+        double zv = 0.0;
+        if (d.pitch != 0.0) {
+            const double dphi = (double)v * (d.angle_span / (double)d.nviews) - 0.5 * d.angle_span;
+            zv = d.pitch * d.nt * d.dt * dphi / (2.0 * M_PI);
+        }
+        double oz = 0.5 * d.nz - d.offset_z / d.dz + zv / d.dz;
         double ozi = floor(oz);
         r.oz_i = (int)ozi;
         r.oz_f = (float)(oz - ozi);
@@ -188,6 +194,8 @@ static int validate(const oslalm_geom_desc *d) {
     if (d->kind < 0 || d->kind > 2) return fail(OSLALM_ERR_ARG, "unknown geometry kind %d", d->kind);
     if (d->nx <= 0 || d->ny <= 0 || d->nz <= 0 || d->nviews <= 0 || d->ns <= 0 || d->nt <= 0)
         return fail(OSLALM_ERR_ARG, "sizes must be positive");
+    if (!(d->pitch >= 0.0 && d->pitch < 1e6)) return fail(OSLALM_ERR_ARG, "pitch must be >= 0");
+    if (d->pitch != 0.0 && d->kind != OSLALM_CONE3D_FLAT) return fail(OSLALM_ERR_ARG, "a helix needs the cone beam");
     if (d->kind != OSLALM_CONE3D_FLAT && (d->nz != 1 || d->nt != 1))
         return fail(OSLALM_ERR_ARG, "2D geometries need nz = nt = 1");
     if (!(d->dx > 0 && d->dy > 0 && d->dz > 0 && d->ds > 0 && d->dt > 0))
@@ -374,6 +382,21 @@ int oslalm_geom_destroy(oslalm_geom *g) {
     cudaFree(g->d_views3);
     cudaFree(g->d_allviews);
     delete g;
+    return OSLALM_OK;
+}
+
+int oslalm_max_subsets(const oslalm_geom_desc *d, double s, double *m_max) {
+    clear_error();
+    if (!d || !m_max) return fail(OSLALM_ERR_ARG, "NULL argument");
+    if (!(s > 0.0)) return fail(OSLALM_ERR_ARG, "need s > 0");
+    if (d->nviews <= 0 || !(d->angle_span > 0.0)) return fail(OSLALM_ERR_ARG, "need views over a positive angle");
+    if (d->pitch == 0.0) {
+        *m_max = (double)d->nviews / s;  // Eq. max_M_axial
+    } else {
+        if (!(d->dso > 0.0 && d->dsd > 0.0)) return fail(OSLALM_ERR_ARG, "helix needs dso, dsd > 0");
+        const double per_turn = (double)d->nviews * (2.0 * M_PI / d->angle_span);
+        *m_max = per_turn * d->dso / (d->pitch * s * d->dsd);  // Eq. max_M_helical
+    }
     return OSLALM_OK;
 }
 

@@ -35,7 +35,7 @@ class GeomDesc(ctypes.Structure):
                 ("nviews", ctypes.c_int), ("angle_start", ctypes.c_double), ("angle_span", ctypes.c_double),
                 ("ns", ctypes.c_int), ("nt", ctypes.c_int), ("ds", ctypes.c_double), ("dt", ctypes.c_double),
                 ("offset_s", ctypes.c_double), ("offset_t", ctypes.c_double),
-                ("dso", ctypes.c_double), ("dsd", ctypes.c_double)]
+                ("dso", ctypes.c_double), ("dsd", ctypes.c_double), ("pitch", ctypes.c_double)]
 
 
 class Params(ctypes.Structure):
@@ -91,6 +91,7 @@ def lib():
         "oslalm_profile_iterate": ([_VP, _VP, i, ctypes.POINTER(d), ip, _VP], i),
         "oslalm_fbp": ([_VP, _VP, _VP, i, _VP], i),
         "oslalm_ray_table": ([ctypes.POINTER(GeomDesc), i, _VP, _VP, _VP, _VP], i),
+        "oslalm_max_subsets": ([ctypes.POINTER(GeomDesc), d, ctypes.POINTER(d)], i),
         "oslalm_geom_build_matrix": ([_VP, _VP, _VP], i),
         "oslalm_geom_drop_matrix": ([_VP], i),
         "oslalm_batch_create": ([ctypes.POINTER(_VP), i, ctypes.POINTER(_VP)], i),
@@ -149,6 +150,14 @@ def geom_desc(geom) -> GeomDesc:
     for name, _ in GeomDesc._fields_:
         setattr(d, name, getattr(geom, name))
     return d
+
+
+def max_subsets(geom, s: float) -> float:
+    """Sec. IV-B's largest number of subsets for s views per subset at the
+    central voxel (axial or helical orbit; oslalm_max_subsets)."""
+    out = ctypes.c_double()
+    _check(lib().oslalm_max_subsets(ctypes.byref(geom_desc(geom)), float(s), ctypes.byref(out)), "max_subsets")
+    return out.value
 
 
 def ray_table(geom, view: int):

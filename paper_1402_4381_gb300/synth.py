@@ -22,9 +22,15 @@ own):
 * fan beam, arc detector: the source sits at ``-dso * u``; channel ``c`` has
   angle ``gamma_c = (c - (ns-1)/2 + offset_s) * ds / dsd`` and direction
   ``cos(gamma_c) u + sin(gamma_c) e``;
-* cone beam, flat detector: source at ``(-dso * u, 0)``; cell ``(t, c)`` is
-  centred at ``(dsd - dso) u + s_c e + t_t z`` with
-  ``t_t = (t - (nt-1)/2 + offset_t) * dt``;
+* cone beam, flat detector: source at ``(-dso * u, z_v)``; cell ``(t, c)`` is
+  centred at ``(dsd - dso) u + s_c e + (z_v + t_t) z`` with
+  ``t_t = (t - (nt-1)/2 + offset_t) * dt``; ``z_v = 0`` for a circular orbit;
+  a helical orbit (``pitch > 0``) advances source and detector by
+  ``pitch * nt * dt`` per turn (table feed = pitch x detector height at the
+  detector, the convention under which a central voxel is covered for
+  ``dso / (pitch dsd)`` turns, Sec. IV-B), centred on the scan:
+  ``z_v = pitch * nt * dt * (phi_v - phi_mid) / (2 pi)``, ``phi_mid`` the
+  middle of the angular range;
 * pixels are half-open boxes ``[lo, hi)``: a ray lying exactly on the plane
   between two pixels belongs to the upper one;
 * pixel ``(ix, iy, iz)`` is centred at ``((ix - (nx-1)/2) dx + offset_x, ...)``;
@@ -77,6 +83,7 @@ class Geometry:
     offset_t: float = 0.0  # in units of rows
     dso: float = 0.0
     dsd: float = 0.0
+    pitch: float = 0.0  # helical cone beam: table feed per turn / (nt dt); 0 = circular orbit
 
     @property
     def image_shape(self):
@@ -93,6 +100,14 @@ class Geometry:
 
     def view_angles(self) -> np.ndarray:
         return np.pi * self.view_turns()
+
+    def source_z(self, views=None) -> np.ndarray:
+        """Height of the source (and detector centre) at each view (mm)."""
+        v = np.arange(self.nviews, dtype=np.float64) if views is None else np.asarray(views, dtype=np.float64)
+        if self.pitch == 0.0:
+            return np.zeros_like(v)
+        dphi = v * (self.angle_span / self.nviews) - 0.5 * self.angle_span
+        return self.pitch * self.nt * self.dt * dphi / (2.0 * np.pi)
 
     def as_dict(self):
         return dataclasses.asdict(self)
@@ -147,6 +162,7 @@ def rays(geom: Geometry, views: Sequence[int] | None = None):
         t = (np.arange(geom.nt, dtype=np.float64) - (geom.nt - 1) / 2.0 + geom.offset_t) * geom.dt
         org[..., 0] = (-geom.dso * cu)[:, None, None]
         org[..., 1] = (-geom.dso * su)[:, None, None]
+        org[..., 2] = geom.source_z(views)[:, None, None]
         dd = geom.dsd - geom.dso
         px = dd * cu[:, None, None] - su[:, None, None] * s[None, None, :]
         py = dd * su[:, None, None] + cu[:, None, None] * s[None, None, :]

@@ -130,6 +130,23 @@ def tiny_cone(n: int = 8, nz: int = 4, nviews: int = 8, ns: int = 15, nt: int = 
                     dso=20.0, dsd=35.0)
 
 
+def tiny_helical(n: int = 8, nz: int = 6, nviews: int = 16, ns: int = 15, nt: int = 5, pitch: float = 0.8) -> Geometry:
+    """Two turns of a helical cone-beam orbit over a small volume."""
+    return Geometry(kind=CONE3D_FLAT, nx=n, ny=n, nz=nz, dx=1.0, dy=1.0, dz=0.8, nviews=nviews,
+                    angle_start=0.05, angle_span=4 * math.pi, ns=ns, nt=nt, ds=1.3, dt=1.1,
+                    dso=20.0, dsd=35.0, pitch=pitch)
+
+
+def c2_helical() -> Workload:
+    """Helical cone beam with the detector of the cone workload: 512x512x64
+    voxels (0.9766^2 x 0.625 mm), 888 x 64 cells, 2 turns of 984 views at pitch
+    0.5 (table feed 35 mm per turn), 20 ellipsoids, I0 = 5e4, 26 neighbours,
+    M = 36 (Sec. IV-B's helical maximum for s = 24 is 46)."""
+    w = c2_cone()
+    g = dataclasses.replace(w.geom, nz=64, nviews=2 * 984, angle_span=4 * math.pi, pitch=0.5)
+    return dataclasses.replace(w, name="helical_512x512x64_v1968_c888x64_p0.5_M36", geom=g, M=36, n_iter=20)
+
+
 def c3_batch(n_slices: int = 64, seed: int = 1301, n_iter: int = 30):
     """Batched 2D fan beam: n independent slices, image sizes uniform in
     {256^2, 384^2, 512^2} over a 500 mm field of view, view counts uniform in

@@ -89,3 +89,23 @@ def test_null_handles_are_errors_not_crashes(L):
     assert L.oslalm_rmsd(None, None, None, 0, ctypes.byref(out), None) == -1
     with pytest.raises(oslalm.OslalmError):
         oslalm._check(L.oslalm_subset_order(-3, None), "subset_order")
+
+
+def test_max_subsets_rule_on_the_papers_scanner():
+    """Sec. IV-B with the GE scanner of the paper's experiments (984 views per
+    turn, dso 541 mm, dsd 949 mm): axial 984 views / s = 40 -> 24 (the paper
+    suggests about 24 for the axial GE performance phantom); helical s = 24:
+    pitch 0.5 -> 46 (about 40 for the shoulder), pitch 1.0 -> 23 (about 20 for
+    the abdomen), inversely proportional to the pitch."""
+    import math
+    from paper_1402_4381_gb300 import oslalm, synth
+    ax = synth.Geometry(kind=synth.FAN2D_ARC, nx=8, ny=8, nviews=984, angle_span=2 * math.pi, ns=888,
+                        ds=1.0239, dso=541.0, dsd=949.0)
+    assert math.floor(oslalm.max_subsets(ax, 40)) == 24
+    hel = synth.Geometry(kind=synth.CONE3D_FLAT, nx=8, ny=8, nz=4, nviews=7146, angle_span=7146 / 984 * 2 * math.pi,
+                         ns=888, nt=32, ds=1.0239, dt=1.0963, dso=541.0, dsd=949.0, pitch=0.5)
+    m05 = oslalm.max_subsets(hel, 24)
+    assert abs(m05 - 984 * 541.0 / (0.5 * 24 * 949.0)) < 1e-9 and math.floor(m05) == 46
+    hel.pitch = 1.0
+    assert math.floor(oslalm.max_subsets(hel, 24)) == 23
+    assert abs(oslalm.max_subsets(hel, 24) * 2 - m05) < 1e-9

@@ -26,8 +26,12 @@ def small_cone(nx=40, nz=12, nviews=30, ns=56, nt=14, M=5):
     return W.scaled(W.c2_cone(), nx, nviews, ns, M, name_suffix="small", nz=nz, nt=nt)
 
 
+def small_helical(nx=40, nz=16, nviews=60, ns=56, nt=14, M=5):
+    return W.scaled(W.c2_helical(), nx, nviews, ns, M, name_suffix="small", nz=nz, nt=nt)
+
+
 CASES = [("small", small_cone().geom), ("ragged", small_cone(nx=37, nz=9, nviews=17, ns=45, nt=11).geom),
-         ("tiny", W.tiny_cone())]
+         ("tiny", W.tiny_cone()), ("helical", small_helical().geom), ("tiny_helical", W.tiny_helical())]
 
 
 def _volume(g, seed):
@@ -65,9 +69,10 @@ def test_cone_adjoint(L, name, g):
     assert abs(lhs - rhs) <= ADJ_TOL * abs(lhs)
 
 
-def test_cone_exact_transpose(L):
+@pytest.mark.parametrize("g", [W.tiny_cone(n=6, nz=3, nviews=5, ns=11, nt=5),
+                               W.tiny_helical(n=6, nz=4, nviews=8, ns=11, nt=5)])
+def test_cone_exact_transpose(L, g):
     import torch
-    g = W.tiny_cone(n=6, nz=3, nviews=5, ns=11, nt=5)
     geom = L.Geometry(g)
     npix, nray = int(np.prod(g.image_shape)), int(np.prod(g.sino_shape))
     Af = np.zeros((nray, npix), dtype=np.float32)
@@ -84,11 +89,12 @@ def test_cone_exact_transpose(L):
     assert np.array_equal(Af, Ab)
 
 
-def test_cone_oslalm_matches_oracle(L):
+@pytest.mark.parametrize("orbit", ["circular", "helical"])
+def test_cone_oslalm_matches_oracle(L, orbit):
     """26-neighbour hyperbola, BF16 storage of W (the oracle consumes the same
     quantized weights), FP32 D; 2 iterations with the oracle's restarts."""
     from test_gpu_oslalm import quantize_pow2
-    wl = small_cone(M=5)
+    wl = small_cone(M=5) if orbit == "circular" else small_helical(M=5)
     g = wl.geom
     scan = wl.make_scan()
     y, w = scan["y"], scan["w"]
