@@ -255,6 +255,7 @@ struct oslalm_cnn {
                   *dz = nullptr;
     float *dy = nullptr;
     double *loss = nullptr;
+    int *err = nullptr;  // set by a convolution whose tensor-core wait ran out
     std::vector<void *> allocs;
 };
 
@@ -269,10 +270,30 @@ int conv(const oslalm_cnn *c, const __nv_bfloat16 *in, int ld_in, int coff_in, i
     a.out = out; a.ld_out = ld_out; a.coff_out = coff_out; a.cout = cout;
     a.n = n; a.h = h; a.wd = wd; a.relu = relu;
     const long P = (long)n * h * wd;
-    dim3 grid(nb(P, kBM), cout / kBN);
-    conv3x3_kernel<<<grid, 128, 0, st>>>(a);
+    // output channels per block: the largest power of two <= 256 dividing cout
+    // (tensor-memory columns come in powers of two)
+    int bn = 256;
+    while (cout % bn) bn >>= 1;
+    if (bn < 32 || cin % kBK) return fail(OSLALM_ERR_ARG, "convolution needs channel counts that are multiples of 32");
+    dim3 grid(nb(P, kBM), cout / bn);
+#define OSL_CONV(BN)                                                                                       \
+    do {                                                                                                   \
+        static bool opted = false; /* dynamic shared memory above 48 KB, once */                          \
+        if (!opted) {                                                                                      \
+            OSL_CUDA_TRY(cudaFuncSetAttribute(conv3x3_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                              conv_smem_bytes(BN)));                                       \
+            opted = true;                                                                                  \
+        }                                                                                                  \
+        conv3x3_kernel<BN><<<grid, 128, conv_smem_bytes(BN), st>>>(a, c->err);                            \
+    } while (0)
+    switch (bn) {
+        case 32: OSL_CONV(32); break;
+        case 64: OSL_CONV(64); break;
+        case 128: OSL_CONV(128); break;
+        default: OSL_CONV(256); break;
+    }
+#undef OSL_CONV
     OSL_LAUNCH_CHECK("conv3x3_kernel");
-    (void)c;
     return OSLALM_OK;
 }
 
@@ -481,6 +502,7 @@ int oslalm_cnn_create(int batch, int height, int width, unsigned long long seed,
         if (e == cudaSuccess) c->allocs.push_back(*p);
     };
     const size_t bf = sizeof(__nv_bfloat16);
+    A((void **)&c->err, sizeof(int));
     A((void **)&c->w32, sizeof(float) * o);
     A((void **)&c->grad, sizeof(float) * o);
     A((void **)&c->m, sizeof(float) * o);
@@ -545,6 +567,7 @@ int oslalm_cnn_create(int batch, int height, int width, unsigned long long seed,
     for (int cc = 0; cc < 32; ++cc) h[c->off_ow + cc] = (float)(0.01 * normal());
     e = cudaMemcpy(c->w32, h.data(), sizeof(float) * o, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(c->m, 0, sizeof(float) * o);
+    if (e == cudaSuccess) e = cudaMemset(c->err, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(c->v, 0, sizeof(float) * o);
     int rc = e == cudaSuccess ? refresh_weights(c, nullptr) : fail(OSLALM_ERR_CUDA, "%s", cudaGetErrorString(e));
     if (!rc && (e = cudaDeviceSynchronize()) != cudaSuccess) rc = fail(OSLALM_ERR_CUDA, "%s", cudaGetErrorString(e));

@@ -5,10 +5,11 @@
 // channel offset `coff`), which makes the U-Net's concatenations free.
 //
 // conv3x3_kernel: implicit GEMM  out[p][co] = sum_{tap, ci} in[p + shift(tap)][ci] w[co][tap][ci]
-//   block tile 128 pixels x 32 output channels, K step = one tap x 32 input
-//   channels, double-buffered cp.async staging, ldmatrix + mma.sync
-//   m16n8k16 (bf16 x bf16 -> f32).  With transposed, tap-flipped weights the
-//   same kernel computes the data gradient.
+//   on the tcgen05 tensor cores: block tile 128 pixels x BN output channels
+//   (BN = 32..256) accumulated in tensor memory, K step = one tap x 32 input
+//   channels, double-buffered cp.async staging into the core-matrix layout,
+//   MMAs issued by one thread and tracked by mbarriers.  With transposed,
+//   tap-flipped weights the same kernel computes the data gradient.
 // wgrad3x3_kernel: dW[co][tap][ci] = sum_p dz[p][co] x[p + shift(tap)][ci],
 //   split over pixel ranges, partial tiles added with FP32 atomics.
 #pragma once
@@ -59,23 +60,126 @@ struct ConvArgs {
     int relu;
 };
 
-constexpr int kBM = 128, kBN = 32, kBK = 32, kStride = 40;  // smem row stride (elements): conflict-free ldmatrix
+// ---------------------------------------------------------------- tcgen05 (5th-generation tensor cores)
+// Shared-memory operand tiles in the canonical K-major layout without
+// swizzle: 8 x 8 "core matrices" of 8 rows x 16 bytes stored contiguously
+// (128 bytes); the core matrices of one 8-row group follow each other along K
+// (leading byte offset 128), the 8-row groups follow at the stride byte offset.
+namespace tc {
 
-__global__ void __launch_bounds__(128) conv3x3_kernel(ConvArgs a) {
-    __shared__ __align__(16) __nv_bfloat16 sA[2][kBM * kStride];
-    __shared__ __align__(16) __nv_bfloat16 sB[2][kBN * kStride];
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// bounded: each try suspends for a bounded time, the loop ends in well under a second
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity) {
+    for (int i = 0; i < (1 << 22); ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+__device__ __forceinline__ void fence_barrier_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void fence_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// tensor-memory columns for the accumulator (one warp; a power of two >= 32)
+__device__ __forceinline__ void tmem_alloc(uint32_t *dst, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)), "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+// shared-memory matrix descriptor: start address, leading / stride byte
+// offsets (all >> 4), descriptor version 1, no swizzle
+__device__ __forceinline__ uint64_t smem_desc(const void *p, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((smem_u32(p) >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+// instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both
+// K-major, N >> 3 and M >> 4
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+// D[tmem] (+)= A[smem] x B[smem]^T, issued by one thread
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+// the mbarrier completes once every MMA issued so far by this thread is done
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+// 8 consecutive FP32 columns of this thread's tensor-memory lane
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float *v) {
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+}  // namespace tc
+
+constexpr int kBM = 128, kBK = 32;  // pixels per block; input channels (one tap) per K step
+
+// dynamic shared memory of conv3x3_kernel<BN>: two stages of A (128 x 32) and
+// B (BN x 32) tiles, then two mbarriers and the tensor-memory address
+__host__ __device__ constexpr int conv_smem_bytes(int bn) { return 2 * (kBM + bn) * kBK * 2 + 32; }
+
+// One block: 128 pixels x BN output channels.  Every K step (one tap x 32 input
+// channels) is staged by all threads with cp.async into the core-matrix
+// layout (zero rows outside the image), then one thread issues two
+// 128 x BN x 16 tcgen05 MMAs into the tensor-memory accumulator and commits
+// them to the stage's mbarrier, which the stage's next loads wait for.  The
+// epilogue reads the accumulator row by row (thread = pixel), adds the bias,
+// applies ReLU and stores BF16.  err: set when a wait runs out (the block then
+// stores garbage instead of hanging).
+template <int BN>
+__global__ void __launch_bounds__(128) conv3x3_kernel(ConvArgs a, int *err) {
+    extern __shared__ __align__(1024) unsigned char sm[];
+    constexpr int A_BYTES = kBM * kBK * 2, B_BYTES = BN * kBK * 2;
+    unsigned char *sA = sm, *sB = sm + 2 * A_BYTES;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sm + 2 * (A_BYTES + B_BYTES));
+    uint32_t *s_taddr = reinterpret_cast<uint32_t *>(bar + 2);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const long P = (long)a.n * a.h * a.wd;
     const long p0 = (long)blockIdx.x * kBM;
-    const int co0 = blockIdx.y * kBN;
-    const int nk = 9 * (a.cin / kBK);  // K steps
-    // per-thread A rows: 4 chunks of 16 B -> (row, chunk)
+    const int co0 = blockIdx.y * BN;
+    const int csteps = a.cin / kBK;
+    const int nk = 9 * csteps;
+    if (warp == 0) tc::tmem_alloc(s_taddr, BN);
+    if (tid < 2) tc::mbar_init(&bar[tid], 1);
+    tc::fence_barrier_init();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t taddr = *s_taddr;
     auto load_stage = [&](int ks, int buf) {
-        const int tap = ks / (a.cin / kBK), ci0 = (ks % (a.cin / kBK)) * kBK;
+        const int tap = ks / csteps, ci0 = (ks % csteps) * kBK;
         const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+        unsigned char *A = sA + buf * A_BYTES;
+        unsigned char *B = sB + buf * B_BYTES;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int idx = tid + q * 128;  // 0..511
+        for (int q = 0; q < 4; ++q) {  // 128 rows x 4 chunks of 8 channels
+            const int idx = tid + q * 128;
             const int row = idx >> 2, ch = idx & 3;
             const long p = p0 + row;
             bool ok = p < P;
@@ -89,76 +193,71 @@ __global__ void __launch_bounds__(128) conv3x3_kernel(ConvArgs a) {
                 src = p + (long)dy * a.wd + dx;
             }
             const __nv_bfloat16 *g = a.in + (ok ? src : 0) * a.ld_in + a.coff_in + ci0 + ch * 8;
-            cp_async16(&sA[buf][row * kStride + ch * 8], g, ok);
+            cp_async16(A + (row >> 3) * 512 + ch * 128 + (row & 7) * 16, g, ok);
         }
-        {
-            const int row = tid >> 2, ch = tid & 3;  // 32 rows (co) x 4 chunks
+#pragma unroll
+        for (int q = 0; q < BN / 32; ++q) {  // BN rows x 4 chunks
+            const int idx = tid + q * 128;
+            const int row = idx >> 2, ch = idx & 3;
             const __nv_bfloat16 *g = a.w + ((long)(co0 + row) * 9 + tap) * a.cin + ci0 + ch * 8;
-            cp_async16(&sB[buf][row * kStride + ch * 8], g, co0 + row < a.cout);
+            cp_async16(B + (row >> 3) * 512 + ch * 128 + (row & 7) * 16, g, true);
         }
         cp_async_commit();
     };
-    float acc[2][4][4];
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-#pragma unroll
-            for (int k = 0; k < 4; ++k) acc[i][j][k] = 0.f;
+    bool ok = true;
     load_stage(0, 0);
     for (int ks = 0; ks < nk; ++ks) {
         const int buf = ks & 1;
         if (ks + 1 < nk) {
+            // stage buf ^ 1 was read by the MMAs of step ks - 1
+            if (ks >= 1 && !tc::mbar_wait(&bar[buf ^ 1], ((ks - 1) >> 1) & 1)) ok = false;
             load_stage(ks + 1, buf ^ 1);
             cp_async_wait<1>();
         } else {
             cp_async_wait<0>();
         }
+        tc::fence_proxy_async();  // this thread's staged tiles -> visible to the tensor cores
         __syncthreads();
+        if (tid == 0) {
+            tc::fence_after_sync();
+            const unsigned char *A = sA + buf * A_BYTES, *B = sB + buf * B_BYTES;
 #pragma unroll
-        for (int kk = 0; kk < kBK; kk += 16) {
-            uint32_t af[2][4];
-#pragma unroll
-            for (int mi = 0; mi < 2; ++mi) {
-                const int r = warp * 32 + mi * 16 + (lane & 15);
-                ldsm_x4(af[mi][0], af[mi][1], af[mi][2], af[mi][3], &sA[buf][r * kStride + kk + (lane >> 4) * 8]);
-            }
-            uint32_t bf[4][2];
-#pragma unroll
-            for (int nj = 0; nj < 4; nj += 2) {
-                // two n8 tiles: matrices (n rows 0-7, k0), (n 0-7, k0+8), (n 8-15, k0), (n 8-15, k0+8)
-                const int r = nj * 8 + (lane & 7) + ((lane >> 4) << 3);
-                const int c = kk + ((lane >> 3) & 1) * 8;
-                ldsm_x4(bf[nj][0], bf[nj][1], bf[nj + 1][0], bf[nj + 1][1], &sB[buf][r * kStride + c]);
-            }
-#pragma unroll
-            for (int mi = 0; mi < 2; ++mi)
-#pragma unroll
-                for (int nj = 0; nj < 4; ++nj) mma16816(acc[mi][nj], af[mi], bf[nj][0], bf[nj][1]);
+            for (int kh = 0; kh < kBK / 16; ++kh)
+                tc::mma_bf16(taddr, tc::smem_desc(A + kh * 256, 128, 512), tc::smem_desc(B + kh * 256, 128, 512),
+                             tc::idesc_bf16(kBM, BN), (ks > 0 || kh > 0) ? 1u : 0u);
+            tc::mma_commit(&bar[buf]);
         }
-        __syncthreads();
     }
-    // epilogue: bias, ReLU, BF16 store of pairs of channels
+    if (!tc::mbar_wait(&bar[(nk - 1) & 1], ((nk - 1) >> 1) & 1)) ok = false;
+    if (!ok) atomicOr(err, 1);
+    tc::fence_after_sync();
+    const long p = p0 + warp * 32 + lane;  // this thread's accumulator row (tensor-memory lane)
+#pragma unroll 1
+    for (int c = 0; c < BN; c += 8) {
+        float v[8];
+        tc::tmem_ld8(taddr + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, v);
+        if (p < P) {
+            const int co = co0 + c;
+            __align__(16) __nv_bfloat162 o[4];
 #pragma unroll
-    for (int mi = 0; mi < 2; ++mi)
-#pragma unroll
-        for (int nj = 0; nj < 4; ++nj)
-#pragma unroll
-            for (int hrow = 0; hrow < 2; ++hrow) {
-                const long p = p0 + warp * 32 + mi * 16 + (lane >> 2) + hrow * 8;
-                const int co = co0 + nj * 8 + (lane & 3) * 2;
-                if (p >= P || co >= a.cout) continue;
-                float v0 = acc[mi][nj][hrow * 2 + 0], v1 = acc[mi][nj][hrow * 2 + 1];
+            for (int i = 0; i < 4; ++i) {
+                float v0 = v[2 * i], v1 = v[2 * i + 1];
                 if (a.bias) {
-                    v0 += a.bias[co];
-                    v1 += a.bias[co + 1];
+                    v0 += a.bias[co + 2 * i];
+                    v1 += a.bias[co + 2 * i + 1];
                 }
                 if (a.relu) {
                     v0 = fmaxf(v0, 0.f);
                     v1 = fmaxf(v1, 0.f);
                 }
-                *reinterpret_cast<__nv_bfloat162 *>(a.out + p * a.ld_out + a.coff_out + co) = __floats2bfloat162_rn(v0, v1);
+                o[i] = __floats2bfloat162_rn(v0, v1);
             }
+            *reinterpret_cast<uint4 *>(a.out + p * a.ld_out + a.coff_out + co) = *reinterpret_cast<const uint4 *>(o);
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(taddr, BN);
 }
 
 struct WgradArgs {
