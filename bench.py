@@ -47,11 +47,13 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-time-to-hu", action="store_true")
-    ap.add_argument("--workload", default="fan", choices=["fan", "fan256", "cone", "helical", "parallel", "batch"],
+    ap.add_argument("--workload", default="fan",
+                    choices=["fan", "fan256", "cone", "helical", "parallel", "batch", "cnn"],
                     help="fan: the 512^2 fan-beam scan (default, the headline); fan256: the same scan family at "
                          "256^2, 492 views, M = 12; cone / parallel: the 512x512x128 cone-beam and 128^2 "
                          "parallel-beam scans; helical: 512x512x64, 2 turns of 984 views at pitch 0.5, M = 36; "
-                         "batch: 64 fan-beam slices of mixed sizes advanced together")
+                         "batch: 64 fan-beam slices of mixed sizes advanced together; cnn: training steps of the "
+                         "warm-start U-Net (batch 8 of 512^2 images)")
     ap.add_argument("--slices", type=int, default=64)
     ap.add_argument("--matrix", action="store_true",
                     help="2D: stream the system matrix held in device memory (oslalm_geom_build_matrix) instead "
@@ -624,8 +626,67 @@ def run_batch(args):
     return 0
 
 
+def run_cnn(args):
+    """Training steps (forward, backward, Adam) of the warm-start U-Net on
+    batches of 8 images of 512^2 pixels: TFLOP/s against the BF16 tensor-core
+    peak, plus the forward pass alone (inference)."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_1402_4381_gb300 import oslalm
+    B, H, Wd = 8, 512, 512
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    gen = torch.Generator(device=dev).manual_seed(0)
+    x = torch.rand((B, H, Wd), device=dev, generator=gen) * 0.04
+    t = x + 0.002 * torch.randn((B, H, Wd), device=dev, generator=gen)
+    scale = 1.0 / 0.0192
+    net = oslalm.WarmStartNet(B, H, Wd, seed=0)
+    fpi = oslalm.WarmStartNet.flops_per_image(H, Wd)
+
+    def timed(fn, n):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(n):
+            fn()
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / n
+
+    sampler = ClockSampler(0)
+    sampler.start()
+    time.sleep(0.3)
+    ms_train = timed(lambda: net.train_step(x, t, scale, 1e-4, want_loss=False), args.steps)
+    ms_fwd = timed(lambda: net.forward(x, scale), args.steps)
+    clocks = sampler.stop()
+    tf_train = 3.0 * fpi * B / (ms_train / 1000.0) / 1e12
+    tf_fwd = fpi * B / (ms_fwd / 1000.0) / 1e12
+    pk = peaks() or {}
+    peak = pk.get("bf16_tflops_sustained", 1700.0)
+    line = {
+        "metric": "warm-start U-Net training throughput (BF16 tensor cores, FP32 accumulation)",
+        "value": tf_train, "unit": "TFLOP/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_train, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
+        "data": "synthetic", "config": {"workload": "unet4_c32_batch8_512x512", "batch": B, "image": [H, Wd],
+                                        "flop_per_image_forward": fpi,
+                                        "l2": "activations of one step (~1 GB) exceed the L2"},
+        "forward_only": {"value": tf_fwd, "unit": "TFLOP/s", "ms_per_batch": ms_fwd},
+        "roofline": {"kernel": "conv3x3_kernel (tcgen05) + wgrad3x3_kernel", "bound": "tensor",
+                     "achieved": tf_train, "peak": peak, "unit": "TFLOP/s", "frac": tf_train / peak,
+                     "traffic": None, "peak_basis": "measured cuBLAS BF16, sustained"},
+        "gpu_launches": None, "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    net.close()
+    return 0
+
+
 def main():
     args = parse()
+    if args.workload == "cnn":
+        return run_cnn(args)
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batch":
