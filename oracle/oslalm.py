@@ -25,6 +25,8 @@ Readings (the paper is silent or ambiguous):
   phi(z) = R(z) + <s, z - x> + rho/2 ||z - x||_D^2 with the separable
   majorizer rho D + D_R(x):
       x+ = max(0, x - (s + grad R(x)) / (rho D + D_R(x)));
+  a pixel whose majorizer is 0 (no ray crosses it and beta = 0: no
+  curvature, no gradient) keeps its value;
 * D_R(x) is the Huber-type SQS curvature of the hyperbola potential,
   omega(t) = psi'(t)/t, evaluated at x; the pairwise separable surrogate puts
   2 beta w_jk omega on each pixel of a pair;
@@ -320,10 +322,12 @@ class OsLalm:
         u_prev, v = x, x
         for i in range(self.n_inner):
             gR, DR = self._reg(v)
+            den = rho * H + DR
+            safe = np.where(den > 0.0, den, 1.0)
             if i == 0:
-                u = x - (s + gR) / (rho * H + DR)
+                u = np.where(den > 0.0, x - (s + gR) / safe, x)
             else:
-                u = v - (gR + s + rho * H * (v - x)) / (rho * H + DR)
+                u = np.where(den > 0.0, v - (gR + s + rho * H * (v - x)) / safe, v)
             if self.nonneg:
                 u = np.maximum(u, 0.0)
             v = u + gam[i] * (u - u_prev)

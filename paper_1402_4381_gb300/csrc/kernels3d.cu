@@ -456,7 +456,7 @@ __global__ void __launch_bounds__(256) update3d_kernel(int nx, int ny, int nz, c
     const float rho = (float)st->rho, rho_d = (float)(st->rho * st->alpha);  // alpha: Barzilai-Borwein scale
     const float s = rho * __ldg(zeta + p) + (1.f - rho) * __ldg(gs + p);
     const float den = rho_d * (load_w(D, p) * __ldg(dscale)) + curv;
-    const float xn = xj - (s + grad) / den;
+    const float xn = den > 0.f ? xj - (s + grad) / den : xj;  // no curvature: unchanged
     xo[p] = fmaxf(xn, 0.f);
 }
 
@@ -481,7 +481,8 @@ __global__ void __launch_bounds__(256) fista3d_kernel(int nx, int ny, int nz, co
     const float s = rho * __ldg(zeta + p) + (1.f - rho) * __ldg(gs + p);
     const float rd = rho_d * (load_w(D, p) * __ldg(dscale));
     const float gphi = fmaf(rd, vj - __ldg(xk + p), s + grad);
-    const float un = fmaxf(vj - gphi / (rd + curv), 0.f);
+    const float den = rd + curv;
+    const float un = fmaxf(den > 0.f ? vj - gphi / den : vj, 0.f);
     uo[p] = un;
     if (vo) vo[p] = fmaf(gamma, un - __ldg(u + p), un);
 }

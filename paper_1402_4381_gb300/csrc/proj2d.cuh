@@ -358,7 +358,7 @@ __device__ __forceinline__ void update_tile(float *tile, int ix0, int iy0, int t
         const size_t p = (size_t)iy * nx + ix;
         const float s = rho * __ldg(zeta + p) + (1.f - rho) * __ldg(gs + p);
         const float den = rho_d * (load_w(D, p) * __ldg(dscale)) + curv;
-        const float xn = xj - (s + grad) / den;
+        const float xn = den > 0.f ? xj - (s + grad) / den : xj;  // no curvature: unchanged
         xo[p] = fmaxf(xn, 0.f);
     }
 }
@@ -387,7 +387,8 @@ __device__ __forceinline__ void fista_tile(float *tile, int ix0, int iy0, int tx
         const float s = rho * __ldg(zeta + p) + (1.f - rho) * __ldg(gs + p);
         const float rd = rho_d * (load_w(D, p) * __ldg(dscale));
         const float gphi = fmaf(rd, vj - __ldg(xk + p), s + grad);
-        const float un = fmaxf(vj - gphi / (rd + curv), 0.f);
+        const float den = rd + curv;
+        const float un = fmaxf(den > 0.f ? vj - gphi / den : vj, 0.f);
         uo[p] = un;
         if (vo) vo[p] = fmaf(gamma, un - __ldg(u + p), un);
     }
