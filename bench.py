@@ -68,6 +68,27 @@ def dist_env():
     return rank, world, local
 
 
+def replica_noise_seed(seed, rank):
+    """Independent replicas on N GPUs: rank r reconstructs its own noise
+    realisation of the same scan (the path has no exchange step)."""
+    return seed + 1000 * rank
+
+
+def max_over_ranks(local_ms, dist, device):
+    """The job's time: the slowest rank's (all ranks get it)."""
+    import torch
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(local_ms)
+    t = torch.tensor([float(local_ms)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(world, steps, units_per_step, t_max_ms):
+    """Units processed by all ranks per second of the slowest rank."""
+    return world * steps * units_per_step / (t_max_ms / 1000.0)
+
+
 class ClockSampler:
     """nvidia-smi samples (200 ms) during the timed region."""
 
@@ -238,8 +259,7 @@ def run_ours(args):
 
     wl = {"fan": W.c1_fan, "fan256": W.c1_fan_256, "cone": W.c2_cone, "helical": W.c2_helical,
           "parallel": W.c0_parallel}[args.workload]()
-    if world > 1:  # independent replicas: a different noise realisation per rank
-        wl.noise_seed += 1000 * rank
+    wl.noise_seed = replica_noise_seed(wl.noise_seed, rank)
     g = wl.geom
     scan = wl.make_scan()
     mask_np = roi_mask(g)
@@ -298,13 +318,9 @@ def run_ours(args):
     if world > 1:
         torch.distributed.barrier()
     clocks = sampler.stop()
-    t_max = total_ms
-    if world > 1:
-        tt = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_max = float(tt.item())
+    t_max = max_over_ranks(total_ms, torch.distributed if world > 1 else None, dev)
     units_per_step = wl.n_iter * wl.M
-    value = world * args.steps * units_per_step / (t_max / 1000.0)
+    value = whole_job_value(world, args.steps, units_per_step, t_max)
 
     # ---- end to end through the C ABI with host buffers
     y_h = torch.as_tensor(scan["y"]).pin_memory()
