@@ -35,7 +35,7 @@ METRIC = "A/A' subset-iters/s (OS-LALM, 2D fan beam 512^2, 984x888, M=24)"
 # DRAM bytes (read + write) per launch of the fan-beam workload's kernels, from
 # one ncu --set full capture of the current kernels on this bench's warm-up
 # launches (cold caches); to be re-taken whenever a kernel changes.
-NCU_DRAM_BYTES_FAN = {"bp2d_kernel": 3.45e6, "fp2d_kernel": 2.44e6, "update2d_kernel": 3.68e6}
+NCU_DRAM_BYTES_FAN = {"bp2d_kernel": 3.46e6, "fp2d_kernel": 2.44e6, "update2d_kernel": 3.68e6}
 UNIT = "subset-iters/s"
 
 
@@ -440,7 +440,7 @@ def run_ours(args):
 def time_to_hu(torch, oslalm, wl, geom, y, w, x0, mask_np, dev, stream,
                thresholds=(20.0, 10.0, 5.0, 2.0, 1.0), max_iter=300,
                schedule=((24, 100), (8, 100), (2, 200)), m1_block=1000, m1_max=12000, m1_tol_hu=2e-3,
-               snap_every=10):
+               snap_every=10, inner_iters=100):
     """Time to reach HU thresholds of RMS difference (field of view) from a
     converged image x*, from the FBP image.
 
@@ -453,7 +453,10 @@ def time_to_hu(torch, oslalm, wl, geom, y, w, x0, mask_np, dev, stream,
     configuration (M subsets, storage types of the workload) from the same
     FBP image for up to max_iter iterations, timing each iteration with CUDA
     events ("configured"); OS-LALM with M > 1 does not converge to x*
-    (Sec. III-A), so its RMS difference levels off, reported as "plateau"."""
+    (Sec. III-A), so its RMS difference levels off, reported as "plateau".
+    The same run with Barzilai-Borwein scaling of the majorizer, and with
+    n = 2 and 5 inner FISTA steps for inner_iters iterations ("inner_sweep":
+    per-iteration device time, one graph launch and synchronisation each)."""
     HU = 0.0192 / 1000.0
     mask = torch.as_tensor(mask_np.astype(np.uint8), device=dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -499,24 +502,35 @@ def time_to_hu(torch, oslalm, wl, geom, y, w, x0, mask_np, dev, stream,
 
     # ---- the configured OS-LALM from the same FBP image, without and with
     # Barzilai-Borwein scaling of the majorizer (supplement Sec. II-A)
-    def configured(bb):
+    def configured(bb, n_inner=1, iters=max_iter):
         prob = oslalm.Problem(geom, y, w, beta=wl.beta, delta=wl.delta, nbr=wl.nbr, M=wl.M,
-                              w_dtype=wl.w_dtype, d_dtype=wl.d_dtype, use_graph=True, bb=bb)
+                              w_dtype=wl.w_dtype, d_dtype=wl.d_dtype, use_graph=True, bb=bb, n_inner=n_inner)
         x = x0.clone()
         t_ms = timed(lambda: prob.init(x))
+        t_iter = 0.0
         curve, reached = [], {}
-        for k in range(1, max_iter + 1):
-            t_ms += timed(lambda: prob.iterate(x, 1))
+        for k in range(1, iters + 1):
+            dt = timed(lambda: prob.iterate(x, 1))
+            t_ms += dt
+            t_iter += dt
             r = oslalm.rmsd(x, xs, mask) / HU
             curve.append(round(r, 3))
             for th in thresholds:
                 if th not in reached and r <= th:
                     reached[th] = {"iterations": k, "seconds": round(t_ms / 1000.0, 5)}
         prob.close()
-        return curve, reached
+        return curve, reached, t_iter / iters
 
-    curve, reached = configured(False)
-    curve_bb, reached_bb = configured(True)
+    curve, reached, ms_it = configured(False)
+    curve_bb, reached_bb, _ = configured(True)
+    # number n of inner FISTA steps of the constrained denoising (Sec. III-A):
+    # more steps per outer iteration against their cost
+    sweep = {}
+    for n_inner in (1, 2, 5):
+        c, r, m = (curve, reached, ms_it) if n_inner == 1 else configured(False, n_inner, inner_iters)
+        sweep[str(n_inner)] = {"ms_per_iteration": round(m, 4),
+                               "thresholds": {f"{th:g}": r.get(th) for th in thresholds},
+                               "rmsd_hu_every_10": c[9:inner_iters:10]}
     one = reached.get(1.0)
     sub_one = sub.get(1.0)
     routes = [(n, r) for n, r in (("configured", one), ("configured_bb", reached_bb.get(1.0)),
@@ -534,6 +548,8 @@ def time_to_hu(torch, oslalm, wl, geom, y, w, x0, mask_np, dev, stream,
                               "plateau_hu": round(float(np.mean(curve_bb[-20:])), 3),
                               "rmsd_hu_every_10": curve_bb[9::10],
                               "note": "the configured run with Barzilai-Borwein scaling of the majorizer"},
+            "inner_sweep": {"iterations_run": inner_iters, "M": wl.M, "n": sweep,
+                            "note": "n inner FISTA steps per subset-iteration (n = 1: the SQS step)"},
             "subset_reduction": {"schedule": ", ".join(stages),
                                  "thresholds": {f"{th:g}": sub.get(th) for th in thresholds},
                                  "seconds_to_1hu": sub_one["seconds"] if sub_one else None,

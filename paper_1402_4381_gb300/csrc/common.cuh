@@ -116,7 +116,8 @@ struct Geo3 {  // kernel-side cone geometry (by value)
 struct __align__(16) RayP {
     float f0, kappa_lo, lrow, kq;
     float n0f, hw;
-    int axis, pad;
+    int axis;
+    float lscale;  // lrow / (2 hw): length per unit of minor span (0 when hw = 0)
 };
 
 struct Geo2 {  // kernel-side 2D geometry (by value)
@@ -179,13 +180,13 @@ bool is_3d(const oslalm_geom *g);
 // The row is entered through the ray's minor position at the row centre,
 // c = b(ia + 1/2), and the half-width hw = |kappa|/2: the row covers minor
 // coordinates [c - hw, c + hw] (width |kappa| <= 1, so at most two pixels).
-// A row inside one pixel gives it the full row length lrow; a row crossing a
-// pixel boundary splits lrow in the ratio of the overlaps (the computed span
-// width hi - lo as the denominator, so the two parts sum to lrow).  This is
-// the exact intersection length of a straight ray with the pixels of the
-// row.  The forward projector (marching along a) and the gather
-// back-projector call this same function, so both directions use
-// bit-identical weights.
+// A row inside one pixel gives it the full row length lrow; a row crossing
+// the pixel boundary jl + 1 gives the first pixel the part of lrow in
+// proportion to its overlap, (jl + 1 - lo) lrow / (2 hw), and the second the
+// rest, so the two parts sum to lrow.  This is the exact intersection
+// length of a straight ray with the pixels of the row.  The forward
+// projector (marching along a) and the back-projectors call this same
+// function, so both directions use bit-identical weights.
 __device__ __forceinline__ float rcp_approx(float v) {
     float r;
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
@@ -204,14 +205,12 @@ __device__ __forceinline__ RowW row_weights(const RayP &r, float ia2, float iah)
     const float fr = __fsub_rn(pq, q);      // exact fraction
     const float c = __fmaf_rn(iah, r.kappa_lo, __fadd_rn(r.f0, fr));  // relative to n0 + q
     const float lo = __fsub_rn(c, r.hw), hi = __fadd_rn(c, r.hw);
-    const float jl = floorf(lo), jh = floorf(hi);
-    const float jl1 = __fadd_rn(jl, 1.f);
+    const float jl = floorf(lo), jl1 = __fadd_rn(jl, 1.f);
     RowW w;
     w.j = __fadd_rn(__fadd_rn(r.n0f, q), jl);
-    const bool split = jl != jh;
-    const float scale = __fmul_rn(r.lrow, rcp_approx(__fsub_rn(hi, lo)));
-    w.w0 = split ? __fmul_rn(__fsub_rn(jl1, lo), scale) : r.lrow;
-    w.w1 = split ? __fmul_rn(__fsub_rn(fminf(hi, __fadd_rn(jl1, 1.f)), jl1), scale) : 0.f;
+    const float part = fminf(__fmul_rn(__fsub_rn(jl1, lo), r.lscale), r.lrow);
+    w.w0 = hi > jl1 ? part : r.lrow;
+    w.w1 = __fsub_rn(r.lrow, w.w0);
     return w;
 }
 

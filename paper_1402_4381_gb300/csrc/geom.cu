@@ -100,7 +100,7 @@ static RayP make_rayp(const Ray2 &r) {
     o.n0f = (float)ray_n0(r.packed);
     o.hw = fabsf(fmaf((float)k, 2.44140625e-4f, 0.5f * r.kappa_lo));
     o.axis = ray_axis(r.packed);
-    o.pad = 0;
+    o.lscale = o.hw > 0.f ? (float)((double)o.lrow / (2.0 * (double)o.hw)) : 0.f;
     return o;
 }
 

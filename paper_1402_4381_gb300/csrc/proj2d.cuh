@@ -52,9 +52,9 @@ __device__ __forceinline__ ACC march2(const Geo2 &g, const RayP &rp, const float
     for (; ia <= ia1; ia += stride, ia2 += d2, iah += d1) {
         const RowW w = row_weights(rp, ia2, iah);
         const int j = (int)w.j;
-        const float *row = x + (size_t)ia * sa;
-        const float x0 = (unsigned)j < (unsigned)Nb ? __ldg(row + (ptrdiff_t)j * sb) : 0.f;
-        const float x1 = (w.w1 != 0.f && (unsigned)(j + 1) < (unsigned)Nb) ? __ldg(row + (ptrdiff_t)(j + 1) * sb) : 0.f;
+        const int k = ia * sa + j * sb;  // 32-bit: images hold at most 4096^2 pixels
+        const float x0 = (unsigned)j < (unsigned)Nb ? __ldg(x + k) : 0.f;
+        const float x1 = (w.w1 != 0.f && (unsigned)(j + 1) < (unsigned)Nb) ? __ldg(x + k + sb) : 0.f;
         acc = fma((ACC)w.w0, (ACC)x0, acc);
         acc = fma((ACC)w.w1, (ACC)x1, acc);
     }

@@ -37,14 +37,15 @@ def _fma32(a, b, c):
 def chords_float32(tab, c, ia, jb):
     """Length of ray c inside pixels (ia, jb) (major, minor indices), with the
     float32 operations of the device code in the same order: the device
-    table's derived constants (k / 4096, n0, the row half-width hw), then the
-    row-centre span and the two-pixel split of each row (the device's
-    approximate reciprocal is replaced by an exact one here)."""
+    table's derived constants (k / 4096, n0, the row half-width hw, the
+    length per unit of minor span lrow / (2 hw)), then the row-centre span
+    and the two-pixel split of each row."""
     f0, kl, lrow = F(tab["f0"][c]), F(tab["kappa_lo"][c]), F(tab["lrow"][c])
     axis, n0, k = decode(tab["packed"][c:c + 1])
     n0, k = int(n0[0]), int(k[0])
     kq = F(F(k) * F(2.0 ** -12))
     hw = np.abs(_fma32(F(k), F(2.0 ** -12), F(F(0.5) * kl)))
+    lscale = F(float(lrow) / (2.0 * float(hw))) if hw > 0 else F(0)
     ia = np.asarray(ia, np.int64)
     ia2 = (2 * ia + 1).astype(F)
     iah = (ia.astype(F) + F(0.5)).astype(F)
@@ -53,14 +54,13 @@ def chords_float32(tab, c, ia, jb):
     fr = (pq - q).astype(F)
     cc = _fma32(iah, kl, (f0 + fr).astype(F))
     lo, hi = (cc - hw).astype(F), (cc + hw).astype(F)
-    jl, jh = np.floor(lo), np.floor(hi)
+    jl = np.floor(lo)
     jl1 = (jl + F(1)).astype(F)
     j = (F(n0) + q).astype(F) + jl
-    split = jl != jh
-    with np.errstate(divide="ignore", invalid="ignore"):
-        scale = (lrow * (F(1) / (hi - lo).astype(F))).astype(F)
-    w0 = np.where(split, ((jl1 - lo).astype(F) * scale).astype(F), lrow)
-    w1 = np.where(split, ((np.minimum(hi, (jl1 + F(1)).astype(F)) - jl1).astype(F) * scale).astype(F), F(0))
+    with np.errstate(over="ignore", invalid="ignore"):
+        part = np.minimum(((jl1 - lo).astype(F) * lscale).astype(F), lrow)
+    w0 = np.where(hi > jl1, part, lrow).astype(F)
+    w1 = (lrow - w0).astype(F)
     d = np.asarray(jb, np.int64).astype(F) - j
     ch = np.where(d == 0, w0, np.where(d == 1, w1, F(0)))
     return ch.astype(np.float64), int(axis[0])
