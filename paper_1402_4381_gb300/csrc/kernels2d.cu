@@ -27,7 +27,11 @@ namespace oslalm {
 // ---------------------------------------------------------------- forward
 // One warp = 4 rays (adjacent channels) x 8 lanes; lane q of a ray takes
 // rows ia0+q, ia0+q+8, ...; the 8 partial sums are combined by shuffles in a
-// fixed order.
+// fixed order.  Warp k of block b takes the rays of group b + k gridDim.x
+// (groups of 4 rays in list order): a block's four groups lie a quarter of
+// the list apart, at different places in the fan, so that long central and
+// short edge rays mix in every block and the SMs, which receive the whole
+// grid at once, get equal work.
 template <int MODE, typename WT>
 __global__ void __launch_bounds__(128) fp2d_kernel(Geo2 g, const float *__restrict__ x, float *__restrict__ out,
                                                    const int *__restrict__ views, int nv,
@@ -35,7 +39,7 @@ __global__ void __launch_bounds__(128) fp2d_kernel(Geo2 g, const float *__restri
                                                    const float *__restrict__ wscale, float gain) {
     const int lane = threadIdx.x & 31;
     const int q = lane >> 2;
-    const int ray = (blockIdx.x * 4 + (threadIdx.x >> 5)) * 4 + (lane & 3);
+    const int ray = (blockIdx.x + (threadIdx.x >> 5) * gridDim.x) * 4 + (lane & 3);
     const bool valid = ray < nv * g.ns;
     float acc = 0.f;
     int lv = 0, c = 0, v = -1;
