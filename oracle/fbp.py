@@ -1,7 +1,7 @@
 """FP64 oracle of the filtered back-projection used for the initial image x0.
 
-TEST INFRASTRUCTURE.  The paper starts every run from an FBP image (Sec. V,
-"initial FBP image") without giving its filter or weights; the reading taken
+TEST INFRASTRUCTURE.  The paper starts every run from an FBP image (Sec. V)
+without giving its filter or weights; the reading taken
 here is the textbook analytic reconstruction (A. C. Kak and M. Slaney,
 Principles of Computerized Tomographic Imaging, ch. 3):
 

@@ -3,8 +3,8 @@
  * INFRASTRUCTURE ONLY -- used by the tests, the smoke check and the CPU
  * baseline of the benchmark; the product path never links it).
  *
- * The paper leaves A unspecified (Sec. IV, Eq. ct_recon: "the system matrix of
- * a CT scan").  Reading taken here: a_ij is the exact length of ray i inside
+ * The paper leaves A unspecified (Sec. IV, Eq. ct_recon names it only as the
+ * scan's system matrix).  Reading taken here: a_ij is the exact length of ray i inside
  * pixel/voxel j (pixel basis, one ray per detector cell through the cell
  * centre), computed by Siddon's algorithm (R. L. Siddon, Med. Phys. 12, 1985):
  * parametrise the ray segment P(a) = P0 + a (P1 - P0), a in [0, 1]; collect the

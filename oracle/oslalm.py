@@ -21,7 +21,7 @@ inner iteration (Sec. III-B).
 
 Readings (the paper is silent or ambiguous):
 * inner constrained denoising with n = 1 FISTA step from the warm start x
-  (Sec. IV-A, Sec. V "n=1 suffices"): one projected gradient step on
+  (Sec. IV-A; Sec. V finds one inner step enough): one projected gradient step on
   phi(z) = R(z) + <s, z - x> + rho/2 ||z - x||_D^2 with the separable
   majorizer rho D + D_R(x):
       x+ = max(0, x - (s + grad R(x)) / (rho D + D_R(x)));
