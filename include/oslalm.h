@@ -344,7 +344,11 @@ int oslalm_batch_shape_info(int shape, int *tile_x, int *tile_y, int *lanes);
  * oslalm_cnn_gradients: loss and parameter gradients (host, exchange layout)
  *   without an update.  oslalm_cnn_train_step: one Adam step on (x, target);
  *   *loss (host, may be NULL; when given the call synchronizes).
- * oslalm_cnn_flops_per_image: multiply-add count x 2 of one forward pass. */
+ * oslalm_cnn_flops_per_image: multiply-add count x 2 of one forward pass.
+ * Errors: the convolutions' tensor-core waits are bounded; one that runs out
+ *   marks the network, and the next call that synchronizes (get_params,
+ *   gradients, train_step with a loss) returns OSLALM_ERR_TIMEOUT and clears
+ *   the mark (the outputs since the previous check are invalid). */
 typedef struct oslalm_cnn oslalm_cnn;
 long oslalm_cnn_param_count(void);
 int oslalm_cnn_create(int batch, int height, int width, unsigned long long seed, oslalm_cnn **out);

@@ -419,6 +419,16 @@ int check_n(const oslalm_cnn *c, int n) {
     return OSLALM_OK;
 }
 
+// After a synchronisation: report (and clear) a tensor-core wait of an
+// earlier convolution that ran out of iterations.
+int check_waits(oslalm_cnn *c) {
+    int flag = 0;
+    OSL_CUDA_TRY(cudaMemcpy(&flag, c->err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (!flag) return OSLALM_OK;
+    OSL_CUDA_TRY(cudaMemset(c->err, 0, sizeof(int)));
+    return fail(OSLALM_ERR_TIMEOUT, "a convolution's tensor-core wait ran out; its output is invalid");
+}
+
 int run_forward(oslalm_cnn *c, const float *x, const float *t, float s, float *y, cudaStream_t st) {
     const long P0 = c->P[0];
     pack_input_kernel<<<nb(P0 * 32, 256), 256, 0, st>>>(x, c->in0, P0, s);
@@ -593,6 +603,7 @@ int oslalm_cnn_get_params(oslalm_cnn *c, float *host) {
     if (!c || !host) return fail(OSLALM_ERR_ARG, "NULL argument");
     std::vector<float> h(c->nparam);
     OSL_CUDA_TRY(cudaMemcpy(h.data(), c->w32, sizeof(float) * c->nparam, cudaMemcpyDeviceToHost));
+    if (int rc = check_waits(c)) return rc;
     copy_params(c, h, host, true);
     return OSLALM_OK;
 }
@@ -627,6 +638,7 @@ int oslalm_cnn_gradients(oslalm_cnn *c, const float *x, const float *t, int n, f
     if (int rc = run_forward(c, x, t, scale, nullptr, st)) return rc;
     if (int rc = backward_net(c, st)) return rc;
     OSL_CUDA_TRY(cudaStreamSynchronize(st));
+    if (int rc = check_waits(c)) return rc;
     if (loss) {
         double l;
         OSL_CUDA_TRY(cudaMemcpy(&l, c->loss, sizeof(double), cudaMemcpyDeviceToHost));
@@ -659,6 +671,7 @@ int oslalm_cnn_train_step(oslalm_cnn *c, const float *x, const float *t, int n, 
         double l;
         OSL_CUDA_TRY(cudaMemcpyAsync(&l, c->loss, sizeof(double), cudaMemcpyDeviceToHost, st));
         OSL_CUDA_TRY(cudaStreamSynchronize(st));
+        if (int rc = check_waits(c)) return rc;
         *loss = l / (double)c->P[0];
     }
     return OSLALM_OK;
