@@ -406,7 +406,7 @@ def run_ours(args):
 
     # ---- time to 1 HU against a converged image (M = 1 continuation, long run)
     ttu = None
-    if not args.no_time_to_hu and g.kind != 2:
+    if not args.no_time_to_hu and g.kind != 2 and rank == 0:  # a study of one scan: rank 0 alone
         ttu = time_to_hu(torch, oslalm, wl, geom, y, w, x0, mask_np, dev, stream)
         ttu["fbp_setup_ms"] = fbp_ms
 
@@ -424,7 +424,7 @@ def run_ours(args):
     }
     if ttu:
         line["time_to_1hu"] = ttu
-    if rank == 0 and not args.no_cpu_baseline and g.kind != 2:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and g.kind != 2:  # the oracle: rank 0 at N = 1
         times = oracle_sample(wl, scan, x0_np, 5)
         t = sum(times[1:])
         line["cpu_baseline"] = {"value": len(times[1:]) / t, "unit": UNIT, "cores": 1, "kind": "oracle",
