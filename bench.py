@@ -349,7 +349,8 @@ def run_ours(args):
         e1.record(stream)
         e1.synchronize()
         e2e_ms += e0.elapsed_time(e1)
-    e2e_value = args.steps * units_per_step / (e2e_ms / 1000.0)
+    e2e_value = whole_job_value(world, args.steps, units_per_step,
+                                max_over_ranks(e2e_ms, torch.distributed if world > 1 else None, dev))
     h2d = y_h.numel() * 4 + w_h.numel() * 4 + x0_h.numel() * 4
     d2h = x_out.numel() * 4
 
