@@ -166,29 +166,6 @@ def intersections_per_subset(geom, M, max_views=24):
     return float(n.sum()) * geom.nviews / len(views) / M
 
 
-def roi_mask(geom):
-    """Field of view: pixels inside the disk every view covers; for the cone
-    beam also voxels that project inside the detector rows from every view."""
-    ix = (np.arange(geom.nx) - (geom.nx - 1) / 2.0) * geom.dx
-    iy = (np.arange(geom.ny) - (geom.ny - 1) / 2.0) * geom.dy
-    Y, X = np.meshgrid(iy, ix, indexing="ij")
-    r = np.sqrt(X * X + Y * Y)
-    if geom.kind == 0:
-        R = geom.ns * geom.ds / 2.0
-    else:
-        R = geom.dso * math.sin(geom.ns * geom.ds / 2.0 / geom.dsd)
-    m2 = (r <= R)[None]
-    if geom.kind != 2:
-        return m2
-    if geom.pitch != 0.0:  # helix: the heights between the first and last source positions
-        zs = geom.source_z()
-        iz = (np.arange(geom.nz) - (geom.nz - 1) / 2.0) * geom.dz
-        return m2 & ((iz >= zs.min()) & (iz <= zs.max()))[:, None, None]
-    iz = (np.arange(geom.nz) - (geom.nz - 1) / 2.0) * geom.dz
-    mag = geom.dsd / np.maximum(geom.dso - r, 1e-9)
-    return m2 & (np.abs(iz)[:, None, None] * mag[None] <= geom.nt * geom.dt / 2.0)
-
-
 def peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -255,14 +232,14 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     else:
         torch.cuda.set_device(0)
-    from paper_1402_4381_gb300 import oslalm, workloads as W
+    from paper_1402_4381_gb300 import oslalm, roi, workloads as W
 
     wl = {"fan": W.c1_fan, "fan256": W.c1_fan_256, "cone": W.c2_cone, "helical": W.c2_helical,
           "parallel": W.c0_parallel}[args.workload]()
     wl.noise_seed = replica_noise_seed(wl.noise_seed, rank)
     g = wl.geom
     scan = wl.make_scan()
-    mask_np = roi_mask(g)
+    mask_np = roi.roi_mask(g)
     dev = torch.device("cuda", torch.cuda.current_device())
     y = torch.as_tensor(scan["y"], device=dev)
     w = torch.as_tensor(scan["w"], device=dev)

@@ -396,10 +396,14 @@ def roi_mask(geom):
     iy = (np.arange(geom.ny) - (geom.ny - 1) / 2.0) * geom.dy + geom.offset_y
     Y, X = np.meshgrid(iy, ix, indexing="ij")
     r = np.sqrt(X * X + Y * Y)
-    if geom.kind == 0:
-        R = geom.ns * geom.ds / 2.0
-    else:
-        R = geom.dso * math.sin(geom.ns * geom.ds / 2.0 / geom.dsd)
+    # lateral positions of the outer edges of the first and last detector cell
+    s_edge = np.array([-geom.ns / 2.0 + geom.offset_s, geom.ns / 2.0 + geom.offset_s]) * geom.ds
+    if geom.kind == 0:  # parallel: the band between the edge rays
+        R = float(np.min(np.abs(s_edge)))
+    elif geom.kind == 1:  # arc detector: the edge rays leave the source at angle s / dsd
+        R = geom.dso * float(np.min(np.sin(np.abs(s_edge) / geom.dsd)))
+    else:  # flat detector: at angle atan(s / dsd)
+        R = geom.dso * float(np.min(np.sin(np.arctan(np.abs(s_edge) / geom.dsd))))
     m2 = r <= R
     if geom.kind != 2:
         return m2[None]

@@ -36,7 +36,7 @@ import time
 
 import numpy as np
 
-from . import synth, workloads as W
+from . import roi, synth, workloads as W
 
 SCALE = 1.0 / synth.MU_WATER  # network units: water = 1
 HU = synth.HU
@@ -75,15 +75,6 @@ def make_scans(wls, workers=None):
         return [_scan(w) for w in wls]
     with cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
         return list(ex.map(_scan, wls, chunksize=4))
-
-
-def fov_mask(g):
-    """Pixels inside the scanned field of view (radius dso sin(fan half-angle))."""
-    ix = (np.arange(g.nx) - (g.nx - 1) / 2.0) * g.dx
-    iy = (np.arange(g.ny) - (g.ny - 1) / 2.0) * g.dy
-    Y, X = np.meshgrid(iy, ix, indexing="ij")
-    R = g.dso * math.sin(g.ns * g.ds / 2.0 / g.dsd)
-    return (np.sqrt(X * X + Y * Y) <= R)[None]
 
 
 def _problem(oslalm, torch, geomh, wl, y, w, M=None, use_graph=True):
@@ -249,7 +240,7 @@ def experiment(n_train=2000, n_test=100, target_iters=200, epochs=30, batch=8, l
     xstars = run_batched(oslalm, torch, geomh, wls_te, scans_te, [x.clone() for x in x0_te], ref_schedule, chunk)
     t_ref = time.time() - t0
     log(f"references: {t_ref:.1f} s")
-    mask = fov_mask(g)
+    mask = roi.roi_mask(g)
     fbp_rows = evaluate(oslalm, torch, geomh, wls_te, scans_te, x0_te, xstars, mask, None, n_eval_iter)
     cnn_rows = evaluate(oslalm, torch, geomh, wls_te, scans_te, x0_te, xstars, mask, cnn_init, n_eval_iter)
     return {

@@ -48,32 +48,3 @@ def test_intersection_count_scales_with_subsets():
     g = _generic_fan()
     one = bench.intersections_per_subset(g, 1, max_views=g.nviews)
     assert bench.intersections_per_subset(g, 7, max_views=g.nviews) == pytest.approx(one / 7)
-
-
-def _channel_of_pixels(g, view):
-    """Detector channel coordinate (fractional index) of every pixel centre
-    seen from the source of `view` (fan) or along its direction (parallel)."""
-    ix = (np.arange(g.nx) - (g.nx - 1) / 2.0) * g.dx
-    iy = (np.arange(g.ny) - (g.ny - 1) / 2.0) * g.dy
-    Y, X = np.meshgrid(iy, ix, indexing="ij")
-    phi = g.angle_start + view * g.angle_span / g.nviews
-    cu, su = math.cos(phi), math.sin(phi)
-    if g.kind == synth.PAR2D:
-        s = -X * su + Y * cu
-    else:
-        a = X * cu + Y * su + g.dso
-        b = -X * su + Y * cu
-        s = np.arctan2(b, a) * g.dsd
-    return s / g.ds + (g.ns - 1) / 2.0 - g.offset_s
-
-
-@pytest.mark.parametrize("wl", [W.scaled(W.c1_fan(), 64, 96, 111, 6), W.c0_parallel()])
-def test_field_of_view_pixels_are_seen_by_every_view(wl):
-    g = wl.geom
-    mask = bench.roi_mask(g)[0]
-    seen = np.ones_like(mask)
-    for v in range(g.nviews):
-        c = _channel_of_pixels(g, v)
-        seen &= (c >= -0.5) & (c <= g.ns - 0.5)
-    assert mask.sum() > 0.5 * mask.size
-    assert not np.any(mask & ~seen)  # every masked pixel centre is on every view's detector

@@ -1,8 +1,8 @@
 """Host-side evaluation of the learned warm start, on the CPU: the per-scan
 threshold bookkeeping (scans reaching each HU threshold, mean iterations and
 seconds) and the paired comparison over the scans both starts reach, on
-hand-made curves whose answers are worked out below; the held-out scans'
-field of view; and the scan family's seeding."""
+hand-made curves whose answers are worked out below; and the scan family's
+seeding."""
 import numpy as np
 import pytest
 
@@ -45,17 +45,6 @@ def test_paired_gain_uses_scans_both_starts_reach():
     # 5 HU: only the network, on scan 0
     assert (p["5"]["scans_both"], p["5"]["scans_only_cnn"]) == (0, 1)
     assert p["5"]["iterations_fbp"] is None and p["5"]["seconds_cnn"] is None
-
-
-def test_field_of_view_is_the_scanned_disk():
-    base = WS.base_workload(nx=64, nviews=96, ns=111, M=6)
-    g = base.geom
-    m = WS.fov_mask(g)[0]
-    R = g.dso * np.sin(g.ns * g.ds / 2.0 / g.dsd)
-    assert m[g.ny // 2, g.nx // 2]
-    assert not m[0, 0]  # the corners lie outside the fan's circle
-    area = m.sum() * g.dx * g.dy
-    assert area == pytest.approx(np.pi * R * R, rel=0.05)
 
 
 def test_scan_family_is_seeded_and_distinct():
