@@ -32,10 +32,6 @@ sys.path.insert(0, ROOT)
 
 METRIC = "A/A' subset-iters/s (OS-LALM, 2D fan beam 512^2, 984x888, M=24)"
 
-# DRAM bytes (read + write) per launch of the fan-beam workload's kernels, from
-# one ncu --set full capture of the current kernels on this bench's warm-up
-# launches (cold caches); to be re-taken whenever a kernel changes.
-NCU_DRAM_BYTES_FAN = {"bp2d_kernel": 3.46e6, "fp2d_kernel": 2.44e6, "update2d_kernel": 3.68e6}
 UNIT = "subset-iters/s"
 
 
@@ -55,9 +51,6 @@ def parse():
                          "batch: 64 fan-beam slices of mixed sizes advanced together; cnn: training steps of the "
                          "warm-start U-Net (batch 8 of 512^2 images)")
     ap.add_argument("--slices", type=int, default=64)
-    ap.add_argument("--matrix", action="store_true",
-                    help="2D: stream the system matrix held in device memory (oslalm_geom_build_matrix) instead "
-                         "of evaluating the projector's lengths in every launch")
     return ap.parse_args()
 
 
@@ -173,13 +166,93 @@ def peaks():
         return None
 
 
+# DRAM bytes (read + write) per launch of the fan-beam workload's kernels from
+# one ncu capture, keyed by a hash of the 2D kernel sources it was taken on:
+# when the sources change, the figure no longer describes the kernel and the
+# bench reports traffic as null until a new capture is recorded here.
+NCU_DRAM_FAN = {"sources": None, "bytes": {}}
+KERNEL_SOURCES_2D = ("kernels2d.cu", "proj2d.cuh", "kernels_common.cuh", "common.cuh")
+
+
+def kernel_sources_hash(names=KERNEL_SOURCES_2D):
+    import hashlib
+    h = hashlib.sha256()
+    for n in names:
+        with open(os.path.join(ROOT, "paper_1402_4381_gb300", "csrc", n), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def roofline_record(torch, dev, wl, prof, graph_ms_sub, clocks, workload):
+    """Roofline of the dominant kernel from the per-launch CUDA-event times.
+
+    Work per launch (one subset): the projectors evaluate `inter` (ray,
+    pixel) intersections, 3 FP32 operations each (crossing, length,
+    multiply-add), against the FP32 issue peak (SMs x 128 lanes x the median
+    SM clock sampled in the timed region); their algorithmic HBM bytes are
+    the data a launch must read and write once: forward + residual reads x,
+    y_m, w_m and writes r; back-projection + split gradient reads r and
+    reads and writes zeta and g.  The update reads x, zeta, g, D and writes
+    x+.  `achieved` uses the event times as measured; per_kernel_ms takes
+    off each launch the same share of the gap between their sum and the
+    graph-timed subset-iteration (launch and event overhead)."""
+    g = wl.geom
+    nl = prof["launches"][0]
+    ev = {"update": prof["update"] / nl, "forward": prof["forward"] / nl, "backproject": prof["backproject"] / nl}
+    overhead = max(0.0, (sum(ev.values()) - graph_ms_sub) / 3.0)
+    per = {k: v - overhead for k, v in ev.items()}
+    dom = max(ev, key=ev.get)
+    pk = peaks() or {}
+    hbm = pk.get("hbm_gbs", 6800.0) * 1e9
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_mhz = clocks.get("sm_mhz") or 2070.0
+    npix = g.nx * g.ny * g.nz
+    rays = g.nviews / wl.M * g.nt * g.ns
+    wb = 4 if wl.w_dtype == "f32" else 2
+    db = 4 if wl.d_dtype == "f32" else 2
+    nbytes = {"forward": 4 * npix + rays * (4 + wb + 4), "backproject": rays * 4 + 16 * npix,
+              "update": (4 + 4 + 4 + db + 4) * npix}
+    dim = "3d" if g.kind == 2 else "2d"
+    names = {"forward": f"fp{dim}_kernel", "backproject": f"bp{dim}_kernel", "update": f"update{dim}_kernel"}
+    t = ev[dom] / 1000.0
+    traffic = None
+    if workload == "fan" and NCU_DRAM_FAN["sources"] == kernel_sources_hash():
+        traffic = NCU_DRAM_FAN["bytes"].get(names[dom])
+    hbm_rec = {"achieved": nbytes[dom] / t / 1e9, "peak": hbm / 1e9, "unit": "GB/s", "frac": nbytes[dom] / t / hbm,
+               "algorithmic_bytes": nbytes[dom], "peak_basis": "measured copy bandwidth (MEASURED_PEAKS.json)"}
+    if dom in ("forward", "backproject"):
+        inter = intersections_per_subset(g, wl.M)
+        peak_ops = sms * 128 * sm_mhz * 1e6
+        achieved = 3.0 * inter / t
+        roof = {"kernel": names[dom], "bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
+                "unit": "TFLOP/s", "frac": achieved / peak_ops, "traffic": traffic,
+                "work_per_launch": f"{inter:.4g} intersections x 3 FP32 ops",
+                "peak_basis": f"{sms} SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz (median SM clock under load)",
+                "hbm": hbm_rec, "intersections_per_s": inter / t}
+    else:
+        roof = {"kernel": names[dom], "bound": "hbm", "achieved": hbm_rec["achieved"], "peak": hbm / 1e9,
+                "unit": "GB/s", "frac": hbm_rec["frac"], "traffic": traffic,
+                "work_per_launch": f"{nbytes[dom] / 1e6:.2f} MB", "peak_basis": hbm_rec["peak_basis"]}
+    roof["per_kernel_ms_events"] = {k: round(v, 5) for k, v in ev.items()}
+    roof["per_kernel_ms"] = {k: round(v, 5) for k, v in per.items()}
+    roof["graph_ms_per_subset_iteration"] = round(graph_ms_sub, 5)
+    roof["launch_overhead_ms"] = round(overhead, 5)
+    roof["kernel_sources"] = kernel_sources_hash()
+    return roof
+
+
 # ---------------------------------------------------------------------------- reference arm: the FP64 oracle
 
-def oracle_sample(wl, scan, x0, n_steps):
-    """Time the FP64 oracle's subset-iterations on the workload: returns
-    (seconds per subset-iteration list, description)."""
+ORACLE_SAMPLE_NOTE = ("FP64 oracle subset-iterations (41 views x 888 rays each) of the same scan; for timing only, "
+                      "its majorizer D is approximated from one subset (M A_0'W_0 A_0 1)")
+
+
+def oracle_sample(wl, scan, x0, n_steps, threads=1):
+    """Time the FP64 oracle's subset-iterations on the workload with
+    `threads` host threads in its projector: seconds per subset-iteration."""
     from oracle import oslalm as O
     from oracle import siddon
+    siddon.set_threads(threads)
     g = wl.geom
     data, _ = O.ct_subset_data(g, scan["y"].astype(np.float64), scan["w"].astype(np.float64), wl.M, siddon)
     # timing sample only: D approximated from one subset (M A_0' W_0 A_0 1)
@@ -195,6 +268,20 @@ def oracle_sample(wl, scan, x0, n_steps):
     return times
 
 
+def cpu_baseline(wl, scan, x0):
+    """The oracle on all host cores (8 subset-iterations after one untimed)
+    and on one core (2 after one untimed)."""
+    cores = os.cpu_count() or 1
+    times = oracle_sample(wl, scan, x0, 9, threads=cores)
+    t = sum(times[1:])
+    one = oracle_sample(wl, scan, x0, 3, threads=1)
+    t1 = sum(one[1:])
+    return {"value": 8 / t, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"8 {ORACLE_SAMPLE_NOTE}, {cores} threads, after one untimed",
+            "single_thread": {"value": 2 / t1, "unit": UNIT, "cores": 1,
+                              "sample": "2 of the same subset-iterations, one thread, after one untimed"}}
+
+
 def run_reference(args):
     rank, world, local = dist_env()
     if rank != 0:
@@ -205,7 +292,8 @@ def run_reference(args):
     scan = wl.make_scan()
     from oracle import fbp as ofbp
     x0 = np.maximum(ofbp.fbp(wl.geom, scan["y"].astype(np.float64)), 0.0)
-    times = oracle_sample(wl, scan, x0, args.warmup + args.steps)
+    cores = os.cpu_count() or 1
+    times = oracle_sample(wl, scan, x0, args.warmup + args.steps, threads=cores)
     t = sum(times[args.warmup:])
     value = args.steps / t
     line = {
@@ -213,8 +301,8 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * t / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": wl.name, "step": "one subset-iteration of the FP64 oracle", "M": wl.M},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"{args.steps} timed subset-iterations (41 views x 888 rays), single thread"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{args.steps} timed {ORACLE_SAMPLE_NOTE}, {cores} threads"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -244,13 +332,6 @@ def run_ours(args):
     y = torch.as_tensor(scan["y"], device=dev)
     w = torch.as_tensor(scan["w"], device=dev)
     geom = oslalm.Geometry(g)
-    matrix = None
-    if g.kind != 2 and args.matrix:  # set-up: the system matrix held in device memory
-        t0 = time.perf_counter()
-        geom.build_matrix()
-        torch.cuda.synchronize()
-        matrix = {"forward_bytes": geom.matrix_bytes[0], "backprojection_bytes": geom.matrix_bytes[1],
-                  "build_s": round(time.perf_counter() - t0, 3)}
     # initial image: FBP of the log sinogram, clipped to x >= 0 (set-up)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
@@ -335,52 +416,8 @@ def run_ours(args):
     x.copy_(x0)
     prob.init(x)
     prof = prob.profile_iterate(x, 4 if g.kind != 2 else 1)
-    nl = prof["launches"][0]
-    per = {"update": prof["update"] / nl, "forward": prof["forward"] / nl, "backproject": prof["backproject"] / nl}
-    dom = max(per, key=per.get)
-    pk = peaks()
-    inter = intersections_per_subset(g, wl.M)
-    sm_mhz = clocks.get("sm_mhz") or 2070.0
-    if dom in ("forward", "backproject") and matrix:
-        # the stored lengths of one subset (its share of the layout) plus the
-        # sinogram and image data the kernel reads and writes
-        nvs = g.nviews / wl.M
-        rays = nvs * g.ns * g.nt
-        npix = g.nx * g.ny * g.nz
-        wb = 4 if wl.w_dtype == "f32" else 2
-        if dom == "forward":
-            nbytes = matrix["forward_bytes"] * nvs / g.nviews + rays * (4 + wb + 4) + 4 * npix
-            kname = "fp2d_table_kernel"
-        else:
-            nbytes = matrix["backprojection_bytes"] * nvs / g.nviews + rays * 4 + 16 * npix
-            kname = "bp2d_kernel (matrix)"
-        achieved = nbytes / (per[dom] / 1000.0)
-        hbm = (pk or {}).get("hbm_gbs", 6800.0) * 1e9
-        roof = {"kernel": kname, "bound": "hbm", "achieved": achieved / 1e9, "peak": hbm / 1e9, "unit": "GB/s",
-                "frac": achieved / hbm, "traffic": NCU_DRAM_BYTES_FAN.get(kname) if args.workload == "fan" else None,
-                "work_per_launch": f"{nbytes / 1e6:.1f} MB (stored lengths of one subset, sinogram and image data)",
-                "intersections_per_s": inter / (per[dom] / 1000.0)}
-    elif dom in ("forward", "backproject"):
-        ops = 3.0 * inter  # FP32 ops per (ray, pixel) pair: crossing, length, multiply-accumulate
-        peak_ops = 152 * 128 * sm_mhz * 1e6
-        achieved = ops / (per[dom] / 1000.0)
-        dim = "3d" if g.kind == 2 else "2d"
-        roof = {"kernel": {"forward": f"fp{dim}_kernel", "backproject": f"bp{dim}_kernel"}[dom], "bound": "alu",
-                "achieved": achieved / 1e12, "peak": peak_ops / 1e12, "unit": "TFLOP/s",
-                "frac": achieved / peak_ops,
-                "traffic": NCU_DRAM_BYTES_FAN.get({"forward": "fp2d_kernel", "backproject": "bp2d_kernel"}[dom])
-                if args.workload == "fan" else None,
-                "work_per_launch": f"{inter:.4g} intersections x 3 FP32 ops",
-                "peak_basis": f"152 SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz (median SM clock under load)"}
-    else:
-        bytes_px = 4 + 4 + 4 + (4 if wl.d_dtype == "f32" else 2) + 4  # x, zeta, g, D read; x+ write
-        traffic = bytes_px * g.nx * g.ny * g.nz
-        achieved = traffic / (per[dom] / 1000.0)
-        hbm = (pk or {}).get("hbm_gbs", 6800.0) * 1e9
-        roof = {"kernel": "update3d_kernel" if g.kind == 2 else "update2d_kernel", "bound": "hbm", "achieved": achieved / 1e9, "peak": hbm / 1e9,
-                "unit": "GB/s", "frac": achieved / hbm,
-                "traffic": NCU_DRAM_BYTES_FAN["update2d_kernel"] if args.workload == "fan" else None}
-    roof["per_kernel_ms"] = {k: round(v, 5) for k, v in per.items()}
+    graph_ms_sub = t_max / args.steps / units_per_step  # graph replay, per subset-iteration
+    roof = roofline_record(torch, dev, wl, prof, graph_ms_sub, clocks, args.workload)
 
     # ---- time to 1 HU against a converged image (M = 1 continuation, long run)
     ttu = None
@@ -395,7 +432,7 @@ def run_ours(args):
         "config": {"workload": wl.name, "image": [g.nx, g.ny], "views": g.nviews, "channels": g.ns, "M": wl.M,
                    "iterations_per_step": wl.n_iter, "storage": {"W": wl.w_dtype, "D": wl.d_dtype},
                    "parallelism": f"replicas{world}", "l2": "flushed between timed steps (256 MB write)",
-                   "system_matrix": matrix or "evaluated in every launch"},
+                   "system_matrix": "evaluated in every launch"},
         "gpu_launches": args.steps * (wl.n_iter * wl.M * 3 + 3),
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "roofline": roof, "clocks": clocks,
@@ -403,16 +440,48 @@ def run_ours(args):
     if ttu:
         line["time_to_1hu"] = ttu
     if rank == 0 and world == 1 and not args.no_cpu_baseline and g.kind != 2:  # the oracle: rank 0 at N = 1
-        times = oracle_sample(wl, scan, x0_np, 5)
-        t = sum(times[1:])
-        line["cpu_baseline"] = {"value": len(times[1:]) / t, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                "sample": "4 subset-iterations (41 views x 888 rays) of the same scan, FP64, "
-                                          "single thread, after one untimed"}
+        line["cpu_baseline"] = cpu_baseline(wl, scan, x0_np)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+XSTAR_TOL_HU = 0.1  # the two limits of x* must agree to a tenth of the 1 HU target
+
+
+def verify_converged(torch, oslalm, wl, geom, y, w, xs, xs_b, mask, HU):
+    """Checks of the converged image x* (Sec. III-A: the one-subset method
+    converges to the minimiser of Eq. ct_recon over x >= 0):
+    * KKT: the gradient A'W(Ax - y) + grad R(x) (oslalm_gradient), projected
+      on the constraint (at x = 0 only its negative part), relative to
+      |A'Wy|_inf (the gradient at x = 0), max over the field of view;
+    * the projected SQS step x - max(0, x - grad / D) in HU (RMS and max
+      over the field of view): what one more rho = 1, M = 1 step would move;
+    * the cost (FP64 reductions) and the RMS difference to the limit of the
+      same schedule from another initial image; x* is accepted when that
+      difference is below XSTAR_TOL_HU."""
+    pk = oslalm.Problem(geom, y, w, beta=wl.beta, delta=wl.delta, nbr=wl.nbr, M=1, use_graph=False)
+    pk.init(xs)
+    D = pk.denominator()
+    m = mask.bool()
+    scale = float(pk.gradient(torch.zeros_like(xs)).abs().max())
+    out = {}
+    for name, x in (("x_star", xs), ("second_limit", xs_b)):
+        gr = pk.gradient(x)
+        pg = torch.where(x > 0, gr, torch.clamp(gr, max=0.0))
+        step = x - torch.clamp(x - gr / D, min=0.0)
+        out[name] = {"kkt_rel": float(pg[m].abs().max()) / scale,
+                     "sqs_step_hu_rms": float(step[m].square().mean().sqrt()) / HU,
+                     "sqs_step_hu_max": float(step[m].abs().max()) / HU,
+                     "cost": pk.cost(x)}
+    pk.close()
+    diff = oslalm.rmsd(xs, xs_b, mask) / HU
+    out["limits_rmsd_hu"] = round(diff, 4)
+    out["tolerance_hu"] = XSTAR_TOL_HU
+    out["accepted"] = bool(diff <= XSTAR_TOL_HU)
+    return out
 
 
 def time_to_hu(torch, oslalm, wl, geom, y, w, x0, mask_np, dev, stream,
@@ -447,29 +516,39 @@ def time_to_hu(torch, oslalm, wl, geom, y, w, x0, mask_np, dev, stream,
         return e0.elapsed_time(e1)
 
     # ---- x* by subset reduction, timed and snapshotted
-    xs = x0.clone()
-    snaps, t_ms, it = [], 0.0, 0  # (iterations, seconds, image)
-    stages = []
-    change = None
-    stage_list = list(schedule) + [(1, m1_max)]
-    for M, n in stage_list:
-        p = oslalm.Problem(geom, y, w, beta=wl.beta, delta=wl.delta, nbr=wl.nbr, M=M, use_graph=True)
-        t_ms += timed(lambda: p.init(xs))
-        done = 0
-        prev = xs.clone()
-        while done < n:
-            k = min(snap_every, n - done)
-            t_ms += timed(lambda: p.iterate(xs, k))
-            done += k
-            it += k
-            snaps.append((it, t_ms / 1000.0, xs.clone()))
-            if M == 1 and done % m1_block == 0:
-                change = oslalm.rmsd(xs, prev, mask) / HU
-                prev = xs.clone()
-                if change < m1_tol_hu:
-                    break
-        stages.append(f"M={M} x {done}")
-        p.close()
+    def converge(x_start, record):
+        """Subset reduction, then the one-subset method until the image
+        changes by less than m1_tol_hu over m1_block iterations."""
+        xc = x_start.clone()
+        snaps, t_ms, it, stages, change = [], 0.0, 0, [], None
+        for M, n in list(schedule) + [(1, m1_max)]:
+            p = oslalm.Problem(geom, y, w, beta=wl.beta, delta=wl.delta, nbr=wl.nbr, M=M, use_graph=True)
+            t_ms += timed(lambda: p.init(xc))
+            done = 0
+            prev = xc.clone()
+            while done < n:
+                k = min(snap_every, n - done)
+                t_ms += timed(lambda: p.iterate(xc, k))
+                done += k
+                it += k
+                if record:
+                    snaps.append((it, t_ms / 1000.0, xc.clone()))
+                if M == 1 and done % m1_block == 0:
+                    change = oslalm.rmsd(xc, prev, mask) / HU
+                    prev = xc.clone()
+                    if change < m1_tol_hu:
+                        break
+            stages.append(f"M={M} x {done}")
+            p.close()
+        return xc, snaps, stages, change
+
+    xs, snaps, stages, change = converge(x0, True)
+    # the same from a second start (water over the field of view): the two
+    # limits bound how far either is from the minimiser
+    xs_b, _, stages_b, _ = converge(torch.where(mask.bool(), 0.0192, 0.0).to(torch.float32), False)
+    xstar = verify_converged(torch, oslalm, wl, geom, y, w, xs, xs_b, mask, HU)
+    xstar["second_start"] = {"x0": "water (0.0192 /mm) over the field of view", "schedule": ", ".join(stages_b)}
+    del xs_b
     sub = {}
     for k, t, im in snaps:
         r = oslalm.rmsd(im, xs, mask) / HU
@@ -480,9 +559,11 @@ def time_to_hu(torch, oslalm, wl, geom, y, w, x0, mask_np, dev, stream,
 
     # ---- the configured OS-LALM from the same FBP image, without and with
     # Barzilai-Borwein scaling of the majorizer (supplement Sec. II-A)
-    def configured(bb, n_inner=1, iters=max_iter):
+    keep_at = (5, 20, 50)
+
+    def configured(bb, n_inner=1, iters=max_iter, storage=(wl.w_dtype, wl.d_dtype), keep=None):
         prob = oslalm.Problem(geom, y, w, beta=wl.beta, delta=wl.delta, nbr=wl.nbr, M=wl.M,
-                              w_dtype=wl.w_dtype, d_dtype=wl.d_dtype, use_graph=True, bb=bb, n_inner=n_inner)
+                              w_dtype=storage[0], d_dtype=storage[1], use_graph=True, bb=bb, n_inner=n_inner)
         x = x0.clone()
         t_ms = timed(lambda: prob.init(x))
         t_iter = 0.0
@@ -496,10 +577,16 @@ def time_to_hu(torch, oslalm, wl, geom, y, w, x0, mask_np, dev, stream,
             for th in thresholds:
                 if th not in reached and r <= th:
                     reached[th] = {"iterations": k, "seconds": round(t_ms / 1000.0, 5)}
+            if keep is not None and k in keep_at:
+                keep[k] = x.clone()
         prob.close()
         return curve, reached, t_iter / iters
 
-    curve, reached, ms_it = configured(False)
+    kept16, kept32 = {}, {}
+    curve, reached, ms_it = configured(False, keep=kept16)
+    configured(False, iters=max(keep_at), storage=("f32", "f32"), keep=kept32)
+    storage_err = {str(k): round(oslalm.rmsd(kept16[k], kept32[k], mask) / HU, 4) for k in keep_at}
+    del kept16, kept32
     curve_bb, reached_bb, _ = configured(True)
     # number n of inner FISTA steps of the constrained denoising (Sec. III-A):
     # more steps per outer iteration against their cost
@@ -534,6 +621,10 @@ def time_to_hu(torch, oslalm, wl, geom, y, w, x0, mask_np, dev, stream,
                                  "iterations_to_1hu": sub_one["iterations"] if sub_one else None,
                                  "includes": "every stage's oslalm_init (D recomputed) and iterations, FP32 storage; "
                                              "x0 = FBP; resolution 10 iterations"},
+            "storage_error_hu": {"iterations": storage_err,
+                                 "note": f"RMS difference (field of view) between the configured run with "
+                                         f"{wl.w_dtype} W and {wl.d_dtype} D and the same run with FP32 storage"},
+            "xstar": xstar,
             "reference": f"x*: end of the subset-reduction run; change over its last {m1_block} one-subset "
                          f"iterations {change:.4f} HU" if change is not None else "x*: end of the subset-reduction run"}
 

@@ -150,26 +150,6 @@ int oslalm_version(void);
 int oslalm_geom_create(const oslalm_geom_desc *desc, oslalm_geom **out);
 int oslalm_geom_destroy(oslalm_geom *g);
 
-/* The system matrix A of Sec. IV (the exact ray/pixel lengths that the
- * projector pair evaluates) held in device memory, for 2D geometries: every
- * (ray, major row) length pair, evaluated once by the projector's own
- * arithmetic and stored in one layout per direction.  Afterwards
- * oslalm_project, oslalm_backproject and the OS-LALM calls on this geometry
- * stream the stored lengths instead of evaluating them, with bit-identical
- * results.  Owned by the geometry (freed by oslalm_geom_drop_matrix or
- * oslalm_geom_destroy); bytes[host, 2] (may be NULL) receives the sizes of the
- * forward and the back-projection layouts (together about 8 GB for 512^2
- * pixels, 984 views x 888 channels).  Build it before
- * creating problems whose iterations are captured in CUDA graphs (a graph
- * keeps the kernels it was captured with).  Synchronises `stream` (cudaStream_t,
- * NULL = legacy default).  Errors: ARG (NULL handle, 3D geometry), RANGE
- * (more than 65535 views or 2^32 entries, or a geometry outside the layout's
- * assumptions: then no matrix is kept and the evaluating kernels stay in
- * use), ALLOC, CUDA.
- * oslalm_geom_drop_matrix synchronises the device and frees the matrix. */
-int oslalm_geom_build_matrix(oslalm_geom *g, size_t *bytes, void *stream);  /* bytes[2] */
-int oslalm_geom_drop_matrix(oslalm_geom *g);
-
 /* Host-only view of the 2D system model: the per-ray parameters that the
  * projector pair reads for view `view` (arrays [host, ns] each).  Ray c is
  * written along its major index axis a as b(a) = n0 + f0 + a (k/2048 +
@@ -224,14 +204,21 @@ int oslalm_fbp(const oslalm_geom *g, const float *sino, float *x, int clip_nonne
  * real-time pipeline that forbids cudaMalloc after initialisation because it
  * may synchronize the device).  The paper has no counterpart: this is a
  * deployment variant.  The filtered sinogram lives in a fixed 16 MiB buffer
- * (2^22 FP32 samples) that the library holds on every device that loads it
- * until the process exits; nviews*nt*ns above 2^22 returns OSLALM_ERR_RANGE.
- * The call allocates nothing.  Its first call on a device looks up the
- * buffer's device address (cudaGetSymbolAddress) with that device current;
- * make that first call before any stream capture.  All calls share the one
- * buffer and the next call overwrites it: calls whose work overlaps on the
- * GPU (other streams, other host threads) race, so serialize them.  Errors:
+ * (2^22 FP32 samples) inside the library; nviews*nt*ns above 2^22 returns
+ * OSLALM_ERR_RANGE.  The call itself allocates nothing.
+ * The buffer is reserved on a device when the library's FBP code is first
+ * loaded there (the CUDA runtime loads device code lazily), i.e. by the first
+ * oslalm_fbp_noalloc_prepare or oslalm_fbp_noalloc on that device, and stays
+ * until the process exits.  Call oslalm_fbp_noalloc_prepare() once per
+ * device, with that device current, during initialisation: before reserving
+ * your own memory pool and before any stream capture.  It loads the FBP
+ * kernels and looks up the buffer's device address (cudaGetSymbolAddress);
+ * synchronous; errors: CUDA, RANGE (device ordinal >= 64).
+ * All calls share the one buffer and the next call overwrites it: calls whose
+ * work overlaps on the GPU (other streams, other host threads) race, so
+ * serialize them.  The result is bit-identical to oslalm_fbp's.  Errors:
  * ARG, RANGE, CUDA. */
+int oslalm_fbp_noalloc_prepare(void);
 int oslalm_fbp_noalloc(const oslalm_geom *g, const float *sino, float *x, int clip_nonneg, void *stream);
 
 /* ---- PWLS problem and OS-LALM (Eq. os_lalm_iterates, Sec. III-IV) --------
@@ -274,6 +261,14 @@ int oslalm_set_replay(oslalm_problem *p, const int *restarts, int n);
 int oslalm_cost(oslalm_problem *p, const float *x, double *out, void *stream);
 int oslalm_get_state(oslalm_problem *p, float *g, float *zeta, double *rho_l_j, void *stream);
 int oslalm_set_state(oslalm_problem *p, const float *g, const float *zeta, const double *rho_l_j, void *stream);
+
+/* Gradient of the PWLS cost of Sec. IV (Eq. ct_recon) at x:
+ * grad[dev, image] = A'W(Ax - y) + grad R(x), with W as stored (w_dtype),
+ * FP32 projections summed subset by subset.  For optimality (KKT) checks of
+ * a converged image: at a minimiser over x >= 0, grad = 0 where x > 0 and
+ * grad >= 0 where x = 0.  Does not change the iteration state.  Errors: ARG,
+ * CUDA. */
+int oslalm_gradient(oslalm_problem *p, const float *x, float *grad, void *stream);
 
 /* The SQS denominator D = A'WA1 as stored (dequantized to FP32) into
  * d[dev, image]; valid after oslalm_init.  Errors: STATE, CUDA. */
@@ -346,9 +341,15 @@ int oslalm_batch_shape_info(int shape, int *tile_x, int *tile_y, int *lanes);
  *   *loss (host, may be NULL; when given the call synchronizes).
  * oslalm_cnn_flops_per_image: multiply-add count x 2 of one forward pass.
  * Errors: the convolutions' tensor-core waits are bounded; one that runs out
- *   marks the network, and the next call that synchronizes (get_params,
- *   gradients, train_step with a loss) returns OSLALM_ERR_TIMEOUT and clears
- *   the mark (the outputs since the previous check are invalid). */
+ *   marks the network (the block stops issuing work, waits a bounded time for
+ *   its own MMAs, frees its tensor memory and exits without writing its
+ *   outputs), and the next call that synchronizes (get_params, gradients,
+ *   train_step with a loss) returns OSLALM_ERR_TIMEOUT and clears the mark
+ *   (the outputs since the previous check are invalid).
+ * oslalm_cnn_mark_timeout: sets that mark from the host, exactly as a
+ *   convolution whose wait ran out would (synchronous), so that callers can
+ *   test their handling of OSLALM_ERR_TIMEOUT without a device fault.
+ *   Errors: ARG, CUDA. */
 typedef struct oslalm_cnn oslalm_cnn;
 long oslalm_cnn_param_count(void);
 int oslalm_cnn_create(int batch, int height, int width, unsigned long long seed, oslalm_cnn **out);
@@ -361,6 +362,7 @@ int oslalm_cnn_gradients(oslalm_cnn *c, const float *x, const float *target, int
 int oslalm_cnn_train_step(oslalm_cnn *c, const float *x, const float *target, int n, float scale, float lr,
                           double *loss, void *stream);
 double oslalm_cnn_flops_per_image(int height, int width);
+int oslalm_cnn_mark_timeout(oslalm_cnn *c);
 
 /* ---- monitoring ----------------------------------------------------------
  * *out[host] = sqrt(sum_{mask} (x - xref)^2 / count(mask)) over the pixels

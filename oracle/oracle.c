@@ -38,6 +38,23 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Host threads of the projector loops (OpenMP).  The rays of a forward
+ * projection are independent, so its result does not depend on the thread
+ * count; a back-projection sums its views in a fixed number of view groups
+ * (see oracle_backproject), so its result does not either. */
+static int g_threads = 1;
+
+int oracle_set_threads(int n)
+{
+    g_threads = n < 1 ? 1 : n;
+    return g_threads;
+}
+
+int oracle_get_threads(void) { return g_threads; }
 
 typedef struct {
     int kind; /* 0 parallel 2D, 1 fan 2D arc, 2 cone 3D flat */
@@ -200,48 +217,93 @@ static long alpha_capacity(const og_geom *g)
 int oracle_project(const og_geom *g, const double *x, const int *views, int nv, double *out)
 {
     if (check_geom(g)) return -1;
-    int three_d = g->kind == 2;
-    double *alphas = (double *)malloc(sizeof(double) * (size_t)alpha_capacity(g));
-    if (!alphas) return -2;
-    for (int iv = 0; iv < nv; ++iv) {
-        int v = views[iv];
-        if (v < 0 || v >= g->nviews) { free(alphas); return -1; }
-        for (int t = 0; t < g->nt; ++t)
-            for (int c = 0; c < g->ns; ++c) {
-                double P0[3], P1[3];
-                ray_segment(g, v, t, c, P0, P1);
-                fp_ctx f = {x, 0.0};
-                siddon(g, P0, P1, three_d, alphas, fp_visit, &f);
-                out[((long)iv * g->nt + t) * g->ns + c] = f.acc;
-            }
+    for (int iv = 0; iv < nv; ++iv)
+        if (views[iv] < 0 || views[iv] >= g->nviews) return -1;
+    const int three_d = g->kind == 2;
+    const long nrays = (long)nv * g->nt * g->ns;
+    int err = 0;
+#pragma omp parallel num_threads(g_threads)
+    {
+        double *alphas = (double *)malloc(sizeof(double) * (size_t)alpha_capacity(g));
+        if (!alphas) {
+#pragma omp atomic write
+            err = -2;
+        }
+#pragma omp for schedule(dynamic, 64)
+        for (long i = 0; i < nrays; ++i) {
+            if (!alphas) continue;
+            const int c = (int)(i % g->ns);
+            const int t = (int)((i / g->ns) % g->nt);
+            const int iv = (int)(i / ((long)g->ns * g->nt));
+            double P0[3], P1[3];
+            ray_segment(g, views[iv], t, c, P0, P1);
+            fp_ctx f = {x, 0.0};
+            siddon(g, P0, P1, three_d, alphas, fp_visit, &f);
+            out[i] = f.acc;
+        }
+        free(alphas);
     }
-    free(alphas);
-    return 0;
+    return err;
 }
 
-/* img_j = sum_i a_ij sino_i over the rays of the listed views (img overwritten). */
+/* img_j = sum_i a_ij sino_i over the rays of the listed views (img overwritten).
+ * The views are dealt to G groups (list position iv to group iv mod G, G
+ * fixed by the sizes alone); each group scatters its rays, in list order,
+ * into its own image, and the group images are added in group order. */
 int oracle_backproject(const og_geom *g, const double *sino, const int *views, int nv, double *img)
 {
     if (check_geom(g)) return -1;
-    int three_d = g->kind == 2;
-    long npix = (long)g->nx * g->ny * g->nz;
+    for (int iv = 0; iv < nv; ++iv)
+        if (views[iv] < 0 || views[iv] >= g->nviews) return -1;
+    const int three_d = g->kind == 2;
+    const long npix = (long)g->nx * g->ny * g->nz;
+    int G = nv < 32 ? nv : 32;
+    while (G > 1 && (double)G * npix * sizeof(double) > 2.0e9) G /= 2;
     memset(img, 0, sizeof(double) * (size_t)npix);
-    double *alphas = (double *)malloc(sizeof(double) * (size_t)alpha_capacity(g));
-    if (!alphas) return -2;
-    for (int iv = 0; iv < nv; ++iv) {
-        int v = views[iv];
-        if (v < 0 || v >= g->nviews) { free(alphas); return -1; }
-        for (int t = 0; t < g->nt; ++t)
-            for (int c = 0; c < g->ns; ++c) {
-                double P0[3], P1[3];
-                ray_segment(g, v, t, c, P0, P1);
-                bp_ctx b = {img, sino[((long)iv * g->nt + t) * g->ns + c]};
-                if (b.val == 0.0) continue;
-                siddon(g, P0, P1, three_d, alphas, bp_visit, &b);
-            }
+    if (G < 1) return 0;
+    double **part = (double **)calloc((size_t)G, sizeof(double *));
+    if (!part) return -2;
+    int err = 0;
+    part[0] = img;
+    for (int k = 1; k < G; ++k) {
+        part[k] = (double *)calloc((size_t)npix, sizeof(double));
+        if (!part[k]) err = -2;
     }
-    free(alphas);
-    return 0;
+    if (!err) {
+#pragma omp parallel num_threads(g_threads)
+        {
+            double *alphas = (double *)malloc(sizeof(double) * (size_t)alpha_capacity(g));
+            if (!alphas) {
+#pragma omp atomic write
+                err = -2;
+            }
+#pragma omp for schedule(dynamic, 1)
+            for (int k = 0; k < G; ++k) {
+                if (!alphas) continue;
+                for (int iv = k; iv < nv; iv += G)
+                    for (int t = 0; t < g->nt; ++t)
+                        for (int c = 0; c < g->ns; ++c) {
+                            double P0[3], P1[3];
+                            ray_segment(g, views[iv], t, c, P0, P1);
+                            bp_ctx b = {part[k], sino[((long)iv * g->nt + t) * g->ns + c]};
+                            if (b.val == 0.0) continue;
+                            siddon(g, P0, P1, three_d, alphas, bp_visit, &b);
+                        }
+            }
+            free(alphas);
+        }
+    }
+    if (!err && G > 1) {
+#pragma omp parallel for num_threads(g_threads) schedule(static)
+        for (long j = 0; j < npix; ++j) {
+            double acc = img[j];
+            for (int k = 1; k < G; ++k) acc += part[k][j];
+            img[j] = acc;
+        }
+    }
+    for (int k = 1; k < G; ++k) free(part[k]);
+    free(part);
+    return err;
 }
 
 /* Segment end points of every ray of one view, [nt][ns][2][3] (for tests). */

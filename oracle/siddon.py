@@ -34,10 +34,22 @@ def lib():
         L.oracle_project.argtypes = [gp, dp, ip, ctypes.c_int, dp]
         L.oracle_backproject.argtypes = [gp, dp, ip, ctypes.c_int, dp]
         L.oracle_ray_segments.argtypes = [gp, ctypes.c_int, dp]
-        for f in (L.oracle_project, L.oracle_backproject, L.oracle_ray_segments):
+        L.oracle_set_threads.argtypes = [ctypes.c_int]
+        L.oracle_get_threads.argtypes = []
+        for f in (L.oracle_project, L.oracle_backproject, L.oracle_ray_segments, L.oracle_set_threads,
+                  L.oracle_get_threads):
             f.restype = ctypes.c_int
         _lib = L
     return _lib
+
+
+def set_threads(n: int) -> int:
+    """Host threads of the projector loops (results do not depend on it)."""
+    return int(lib().oracle_set_threads(int(n)))
+
+
+def get_threads() -> int:
+    return int(lib().oracle_get_threads())
 
 
 def og(geom) -> OgGeom:

@@ -598,6 +598,14 @@ int oslalm_cnn_destroy(oslalm_cnn *c) {
     return OSLALM_OK;
 }
 
+int oslalm_cnn_mark_timeout(oslalm_cnn *c) {
+    clear_error();
+    if (!c) return fail(OSLALM_ERR_ARG, "network handle is NULL");
+    const int one = 1;
+    OSL_CUDA_TRY(cudaMemcpy(c->err, &one, sizeof(int), cudaMemcpyHostToDevice));
+    return OSLALM_OK;
+}
+
 int oslalm_cnn_get_params(oslalm_cnn *c, float *host) {
     clear_error();
     if (!c || !host) return fail(OSLALM_ERR_ARG, "NULL argument");

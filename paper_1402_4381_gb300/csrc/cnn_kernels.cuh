@@ -151,7 +151,8 @@ __host__ __device__ constexpr int conv_smem_bytes(int bn) { return 2 * (kBM + bn
 // them to the stage's mbarrier, which the stage's next loads wait for.  The
 // epilogue reads the accumulator row by row (thread = pixel), adds the bias,
 // applies ReLU and stores BF16.  err: set when a wait runs out (the block then
-// stores garbage instead of hanging).
+// stops issuing work, leaves its outputs unwritten and exits after a bounded
+// wait for its own MMAs, instead of hanging).
 template <int BN>
 __global__ void __launch_bounds__(128) conv3x3_kernel(ConvArgs a, int *err) {
     extern __shared__ __align__(1024) unsigned char sm[];
@@ -205,12 +206,19 @@ __global__ void __launch_bounds__(128) conv3x3_kernel(ConvArgs a, int *err) {
         cp_async_commit();
     };
     bool ok = true;
+    int last = -1;  // last K step whose MMAs were committed
     load_stage(0, 0);
     for (int ks = 0; ks < nk; ++ks) {
         const int buf = ks & 1;
         if (ks + 1 < nk) {
             // stage buf ^ 1 was read by the MMAs of step ks - 1
-            if (ks >= 1 && !tc::mbar_wait(&bar[buf ^ 1], ((ks - 1) >> 1) & 1)) ok = false;
+            if (ks >= 1) ok = tc::mbar_wait(&bar[buf ^ 1], ((ks - 1) >> 1) & 1);
+            // one decision for the whole block: after a wait that ran out, no
+            // thread may overwrite a stage the tensor cores could still read
+            if (!__syncthreads_and(ok)) {
+                ok = false;
+                break;
+            }
             load_stage(ks + 1, buf ^ 1);
             cp_async_wait<1>();
         } else {
@@ -227,9 +235,22 @@ __global__ void __launch_bounds__(128) conv3x3_kernel(ConvArgs a, int *err) {
                              tc::idesc_bf16(kBM, BN), (ks > 0 || kh > 0) ? 1u : 0u);
             tc::mma_commit(&bar[buf]);
         }
+        last = ks;
     }
-    if (!tc::mbar_wait(&bar[(nk - 1) & 1], ((nk - 1) >> 1) & 1)) ok = false;
-    if (!ok) atomicOr(err, 1);
+    if (ok) ok = tc::mbar_wait(&bar[(nk - 1) & 1], ((nk - 1) >> 1) & 1);
+    if (!__syncthreads_and(ok)) {
+        // A wait ran out: flag the network, skip the epilogue, let the copies
+        // in flight land, give the MMAs committed so far one more bounded wait
+        // (their last commit), then release the tensor memory and return.
+        // The total wait of the block is bounded by three wait limits.
+        if (tid == 0) atomicOr(err, 1);
+        cp_async_wait<0>();
+        if (last >= 0) tc::mbar_wait(&bar[last & 1], (last >> 1) & 1);
+        tc::fence_before_sync();
+        __syncthreads();
+        if (warp == 0) tc::tmem_dealloc(taddr, BN);
+        return;
+    }
     tc::fence_after_sync();
     const long p = p0 + warp * 32 + lane;  // this thread's accumulator row (tensor-memory lane)
 #pragma unroll 1

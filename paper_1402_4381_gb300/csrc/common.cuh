@@ -130,24 +130,6 @@ struct Geo2 {  // kernel-side 2D geometry (by value)
     int fast_atan;           // fan beam: every pixel centre is within 45 degrees of the source's axis
     const RayP *rays;        // [nviews][ns]
     const View2 *views;      // [nviews]
-    // The system matrix held in device memory (all null until built by
-    // oslalm_geom_build_matrix): every (ray, major row) length pair of the
-    // projector pair, laid out once for each direction.
-    //  forward, per ray (v, c): fp_hdr = {first entry, ia0 | nrows << 16, j0,
-    //    (dir < 0) | axis << 1}; fp_ent[first + r] = {w0 bits | (s & 1) << 31,
-    //    w1 bits | (s >> 1) << 31} for row ia0 + r, where the first pixel j of
-    //    the row is j0 + dir * (sum of the steps s of rows 1..r), dir = +-1;
-    //  back-projection, per (view, orientation, 16x16 tile): bp_blk = {first
-    //    entry row, rows}; per lane (strip) bp_hdr = c_first | (d_first + 1) << 16
-    //    | (dir < 0) << 20 | count << 24; entry i of a lane at
-    //    bp_ent[(first row + i) * 32 + lane] = {w0 bits | (s & 1) << 31, w1 bits
-    //    | (s >> 1) << 31} for channel c_first + i, whose first strip pixel is
-    //    d_first + dir * (sum of the steps s of entries 1..i).
-    const uint4 *fp_hdr;
-    const uint2 *fp_ent;
-    const uint2 *bp_blk;
-    const unsigned *bp_hdr;
-    const uint2 *bp_ent;
 };
 
 }  // namespace oslalm
@@ -160,13 +142,6 @@ struct oslalm_geom {
     oslalm::View2 *d_views;   // [nviews]
     oslalm::View3 *d_views3;  // 3D: [nviews]
     int *d_allviews;          // 0..nviews-1
-    // system matrix (2D, optional): see Geo2
-    uint4 *d_fp_hdr;
-    uint2 *d_fp_ent;
-    uint2 *d_bp_blk;
-    unsigned *d_bp_hdr;
-    uint2 *d_bp_ent;
-    size_t matrix_bytes;
     oslalm::Geo2 geo2() const;
     oslalm::Geo3 geo3() const;
 };
@@ -265,7 +240,6 @@ struct UpdateArgs {  // epilogue arguments of the fused back-projection
     const float *dscale;
 };
 
-void free_matrix2d(oslalm_geom *g);  // releases the device system matrix, if any
 int launch_fp2d(const Geo2 &g, const float *x, float *out, const int *views, int nv,
                 int mode, const float *y, WeightRef w, float gain, cudaStream_t st);
 int launch_bp2d(const Geo2 &g, const float *r, float *out, const int *views, int nv,
@@ -284,6 +258,9 @@ int bp3d_blocks(const Geo3 &g);
 int launch_update3d(int nx, int ny, int nz, const float *x, float *xo, const float *zeta, const float *g,
                     const void *D, int d_dtype, const float *dscale, const DevState *st, float beta,
                     float inv_delta, int nbr, int curv_mode, cudaStream_t s);
+// grad += gradient of the regularizer at x (2D images as one slice)
+int launch_reg_grad_add(int nx, int ny, int nz, const float *x, float *grad, float beta, float inv_delta, int nbr,
+                        cudaStream_t s);
 int launch_reg_value3d(int nx, int ny, int nz, const float *x, double beta, double delta, int nbr,
                        double *partials, int *nparts, cudaStream_t s);
 // inner FISTA step i >= 1: (v, x_k, u) -> u+, and v+ unless vo is null

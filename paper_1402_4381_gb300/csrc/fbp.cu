@@ -131,17 +131,15 @@ __global__ void fbp_bp3d_kernel(FbpGeo g, const View2 *__restrict__ views, const
 
 }  // namespace oslalm
 
-using namespace oslalm;
+namespace oslalm {
 
-extern "C" int oslalm_fbp(const oslalm_geom *gm, const float *sino, float *x, int clip_nonneg, void *stream) {
-    clear_error();
-    if (!gm || !sino || !x) return fail(OSLALM_ERR_ARG, "NULL argument");
+constexpr int kFbpMaxChannels = 8192;
+constexpr size_t kFbpFilterMaxShm = sizeof(float) * (3 * (size_t)kFbpMaxChannels - 1);
+
+// Checks the geometry, then filters sino into q (nviews*nt*ns floats of
+// device memory owned by the caller) and back-projects q into x, on `st`.
+static int fbp_run(const oslalm_geom *gm, const float *sino, float *x, int clip_nonneg, float *q, cudaStream_t st) {
     const oslalm_geom_desc &d = gm->d;
-    if (d.kind != OSLALM_PAR2D && fabs(fabs(d.angle_span) - 2.0 * M_PI) > 1e-9)
-        return fail(OSLALM_ERR_ARG, "fan/cone FBP needs a full 360-degree scan");
-    if (d.pitch != 0.0) return fail(OSLALM_ERR_ARG, "FDK needs a circular orbit (pitch 0)");
-    if (d.ns > 8192) return fail(OSLALM_ERR_RANGE, "FBP supports at most 8192 channels");
-    cudaStream_t st = (cudaStream_t)stream;
     FbpGeo g;
     g.kind = d.kind;
     g.nx = d.nx; g.ny = d.ny; g.nz = d.nz; g.nviews = d.nviews; g.ns = d.ns; g.nt = d.nt;
@@ -158,11 +156,12 @@ extern "C" int oslalm_fbp(const oslalm_geom *gm, const float *sino, float *x, in
     if (d.kind == OSLALM_PAR2D) g.scale = (float)(M_PI / d.nviews);
     else if (d.kind == OSLALM_FAN2D_ARC) g.scale = (float)(2.0 * M_PI / d.nviews);
     else g.scale = (float)(0.5 * 2.0 * M_PI / d.nviews);
-    size_t nq = (size_t)d.nviews * d.nt * d.ns;
-    float *q = nullptr;
-    OSL_CUDA_TRY(cudaMallocAsync((void **)&q, nq * sizeof(float), st));
-    size_t shm = sizeof(float) * (3 * (size_t)d.ns - 1);
-    if (shm > 48 * 1024) cudaFuncSetAttribute(fbp_filter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+    const size_t shm = sizeof(float) * (3 * (size_t)d.ns - 1);
+    if (shm > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(fbp_filter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)kFbpFilterMaxShm);
+        if (e != cudaSuccess) return fail(OSLALM_ERR_CUDA, "FBP filter set-up failed: %s", cudaGetErrorString(e));
+    }
     fbp_filter_kernel<<<d.nviews * d.nt, 256, shm, st>>>(g, sino, q);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) {
@@ -171,9 +170,35 @@ extern "C" int oslalm_fbp(const oslalm_geom *gm, const float *sino, float *x, in
         else fbp_bp2d_kernel<<<grid, block, 0, st>>>(g, gm->d_views, q, x, clip_nonneg);
         e = cudaGetLastError();
     }
-    cudaFreeAsync(q, st);
     if (e != cudaSuccess) return fail(OSLALM_ERR_CUDA, "FBP launch failed: %s", cudaGetErrorString(e));
     return OSLALM_OK;
+}
+
+static int fbp_check(const oslalm_geom *gm, const float *sino, const float *x) {
+    if (!gm || !sino || !x) return fail(OSLALM_ERR_ARG, "NULL argument");
+    const oslalm_geom_desc &d = gm->d;
+    if (d.kind != OSLALM_PAR2D && fabs(fabs(d.angle_span) - 2.0 * M_PI) > 1e-9)
+        return fail(OSLALM_ERR_ARG, "fan/cone FBP needs a full 360-degree scan");
+    if (d.pitch != 0.0) return fail(OSLALM_ERR_ARG, "FDK needs a circular orbit (pitch 0)");
+    if (d.ns > kFbpMaxChannels) return fail(OSLALM_ERR_RANGE, "FBP supports at most %d channels", kFbpMaxChannels);
+    return OSLALM_OK;
+}
+
+}  // namespace oslalm
+
+using namespace oslalm;
+
+extern "C" int oslalm_fbp(const oslalm_geom *gm, const float *sino, float *x, int clip_nonneg, void *stream) {
+    clear_error();
+    if (int rc = fbp_check(gm, sino, x)) return rc;
+    const oslalm_geom_desc &d = gm->d;
+    cudaStream_t st = (cudaStream_t)stream;
+    size_t nq = (size_t)d.nviews * d.nt * d.ns;
+    float *q = nullptr;
+    OSL_CUDA_TRY(cudaMallocAsync((void **)&q, nq * sizeof(float), st));
+    const int rc = fbp_run(gm, sino, x, clip_nonneg, q, st);
+    cudaFreeAsync(q, st);
+    return rc;
 }
 
 // ---------------------------------------------------------------------------
@@ -183,7 +208,15 @@ extern "C" int oslalm_fbp(const oslalm_geom *gm, const float *sino, float *x, in
 // initialisation because cudaMalloc may synchronize the device and its
 // latency is unbounded.  oslalm_fbp_noalloc does the same work as oslalm_fbp
 // but keeps the filtered sinogram in the fixed buffer below, which the
-// library owns on every device that loads it, for the life of the process.
+// library owns on every device where it has been prepared, for the life of
+// the process.
+//
+// The buffer lives in this file's own device module.  The CUDA runtime loads
+// a module on a device the first time something in it is used there (lazy
+// loading), and that is when the buffer's 16 MiB are reserved.
+// oslalm_fbp_noalloc_prepare does that loading (and loads the FBP kernels'
+// code) on purpose, so that a caller can do it at start-up, before it
+// reserves its own pool.
 namespace oslalm {
 
 constexpr size_t kFbpStaticFloats = (size_t)1 << 22;  // 16 MiB of FP32 samples
@@ -194,7 +227,8 @@ static float *g_fbp_scratch_ptr[64] = {nullptr};
 
 // Device address of g_fbp_scratch on the current device, looked up once per
 // device with that device current (host code cannot use the symbol itself:
-// on the host it names a stand-in object, not device memory).
+// on the host it names a stand-in object, not device memory).  The first
+// lookup on a device also loads the FBP kernels there.
 static int fbp_scratch_address(float **out) {
     int dev = 0;
     OSL_CUDA_TRY(cudaGetDevice(&dev));
@@ -205,6 +239,14 @@ static int fbp_scratch_address(float **out) {
         cudaError_t e = cudaGetSymbolAddress(&p, g_fbp_scratch);
         if (e != cudaSuccess || !p)
             return fail(OSLALM_ERR_CUDA, "cudaGetSymbolAddress(g_fbp_scratch) failed: %s", cudaGetErrorString(e));
+        cudaFuncAttributes a;
+        if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, fbp_filter_kernel);
+        if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, fbp_bp2d_kernel);
+        if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, fbp_bp3d_kernel);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(fbp_filter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)kFbpFilterMaxShm);
+        if (e != cudaSuccess) return fail(OSLALM_ERR_CUDA, "loading the FBP kernels failed: %s", cudaGetErrorString(e));
         g_fbp_scratch_ptr[dev] = (float *)p;
     }
     *out = g_fbp_scratch_ptr[dev];
@@ -213,15 +255,17 @@ static int fbp_scratch_address(float **out) {
 
 }  // namespace oslalm
 
+extern "C" int oslalm_fbp_noalloc_prepare(void) {
+    clear_error();
+    float *q = nullptr;
+    return fbp_scratch_address(&q);
+}
+
 extern "C" int oslalm_fbp_noalloc(const oslalm_geom *gm, const float *sino, float *x, int clip_nonneg,
                                   void *stream) {
     clear_error();
-    if (!gm || !sino || !x) return fail(OSLALM_ERR_ARG, "NULL argument");
+    if (int rc = fbp_check(gm, sino, x)) return rc;
     const oslalm_geom_desc &d = gm->d;
-    if (d.kind != OSLALM_PAR2D && fabs(fabs(d.angle_span) - 2.0 * M_PI) > 1e-9)
-        return fail(OSLALM_ERR_ARG, "fan/cone FBP needs a full 360-degree scan");
-    if (d.pitch != 0.0) return fail(OSLALM_ERR_ARG, "FDK needs a circular orbit (pitch 0)");
-    if (d.ns > 8192) return fail(OSLALM_ERR_RANGE, "FBP supports at most 8192 channels");
     const size_t nq = (size_t)d.nviews * d.nt * d.ns;
     if (nq > kFbpStaticFloats)
         return fail(OSLALM_ERR_RANGE,
@@ -229,35 +273,7 @@ extern "C" int oslalm_fbp_noalloc(const oslalm_geom *gm, const float *sino, floa
                     "(use oslalm_fbp)", nq, kFbpStaticFloats);
     float *q = nullptr;
     if (int rc = fbp_scratch_address(&q)) return rc;
-    cudaStream_t st = (cudaStream_t)stream;
-    FbpGeo g;
-    g.kind = d.kind;
-    g.nx = d.nx; g.ny = d.ny; g.nz = d.nz; g.nviews = d.nviews; g.ns = d.ns; g.nt = d.nt;
-    g.dx = (float)d.dx; g.dy = (float)d.dy; g.dz = (float)d.dz;
-    g.xc0 = (float)(d.offset_x - (d.nx - 1) / 2.0 * d.dx);
-    g.yc0 = (float)(d.offset_y - (d.ny - 1) / 2.0 * d.dy);
-    g.zc0 = (float)(d.offset_z - (d.nz - 1) / 2.0 * d.dz);
-    g.ds = (float)d.ds; g.dt = (float)d.dt;
-    g.c0 = (float)((d.ns - 1) / 2.0 - d.offset_s);
-    g.t0 = (float)((d.nt - 1) / 2.0 - d.offset_t);
-    g.dso = (float)d.dso; g.dsd = (float)d.dsd;
-    g.a = d.kind == OSLALM_FAN2D_ARC ? (float)(d.ds / d.dsd) : (float)(d.ds * d.dso / d.dsd);
-    g.az = (float)(d.dt * d.dso / d.dsd);
-    if (d.kind == OSLALM_PAR2D) g.scale = (float)(M_PI / d.nviews);
-    else if (d.kind == OSLALM_FAN2D_ARC) g.scale = (float)(2.0 * M_PI / d.nviews);
-    else g.scale = (float)(0.5 * 2.0 * M_PI / d.nviews);
     // every filtered sample is written before it is read, so the buffer's
     // previous contents (left by the last call) need no clearing
-    size_t shm = sizeof(float) * (3 * (size_t)d.ns - 1);
-    if (shm > 48 * 1024) cudaFuncSetAttribute(fbp_filter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
-    fbp_filter_kernel<<<d.nviews * d.nt, 256, shm, st>>>(g, sino, q);
-    cudaError_t e = cudaGetLastError();
-    if (e == cudaSuccess) {
-        dim3 block(32, 8), grid((d.nx + 31) / 32, (d.ny + 7) / 8, d.kind == OSLALM_CONE3D_FLAT ? d.nz : 1);
-        if (d.kind == OSLALM_CONE3D_FLAT) fbp_bp3d_kernel<<<grid, block, 0, st>>>(g, gm->d_views, q, x, clip_nonneg);
-        else fbp_bp2d_kernel<<<grid, block, 0, st>>>(g, gm->d_views, q, x, clip_nonneg);
-        e = cudaGetLastError();
-    }
-    if (e != cudaSuccess) return fail(OSLALM_ERR_CUDA, "FBP launch failed: %s", cudaGetErrorString(e));
-    return OSLALM_OK;
+    return fbp_run(gm, sino, x, clip_nonneg, q, (cudaStream_t)stream);
 }

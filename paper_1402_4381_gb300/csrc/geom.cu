@@ -257,11 +257,6 @@ oslalm::Geo2 oslalm_geom::geo2() const {
     o.fast_atan = d.kind == OSLALM_FAN2D_ARC && rc < 0.99 * d.dso / sqrt(2.0);
     o.rays = d_rays;
     o.views = d_views;
-    o.fp_hdr = d_fp_hdr;
-    o.fp_ent = d_fp_ent;
-    o.bp_blk = d_bp_blk;
-    o.bp_hdr = d_bp_hdr;
-    o.bp_ent = d_bp_ent;
     return o;
 }
 
@@ -375,7 +370,6 @@ int oslalm_ray_table(const oslalm_geom_desc *desc, int view, float *f0, float *k
 int oslalm_geom_destroy(oslalm_geom *g) {
     clear_error();
     if (!g) return OSLALM_OK;
-    free_matrix2d(g);
     cudaFree(g->d_rays);
     cudaFree(g->d_rays3);
     cudaFree(g->d_views);

@@ -68,85 +68,6 @@ __global__ void __launch_bounds__(128) fp2d_kernel(Geo2 g, const float *__restri
     }
 }
 
-// The same forward projection read from the device system matrix (Geo2): the
-// thread mapping and the summation order of fp2d_kernel (lane q of a ray
-// adds rows ia0 + q, ia0 + q + 8, ...).  A row's first pixel is rebuilt from
-// the step bits of the ray's rows: at each pass the ray's 8 lanes hold 8
-// consecutive rows, and each lane adds the steps of its group's lanes up to
-// itself (ballots of the two step bits).  Bit-identical to fp2d_kernel.
-template <int MODE, typename WT>
-__global__ void __launch_bounds__(128) fp2d_table_kernel(Geo2 g, const float *__restrict__ x,
-                                                         float *__restrict__ out, const int *__restrict__ views,
-                                                         int nv, const float *__restrict__ y,
-                                                         const WT *__restrict__ w, const float *__restrict__ wscale,
-                                                         float gain) {
-    const int lane = threadIdx.x & 31;
-    const int q = lane >> 2;
-    const int ray = (blockIdx.x * 4 + (threadIdx.x >> 5)) * 4 + (lane & 3);
-    const bool valid = ray < nv * g.ns;
-    int v = -1;
-    uint4 h = make_uint4(0u, 0u, 0u, 0u);
-    if (valid) {
-        const int lv = ray / g.ns;
-        const int c = ray - lv * g.ns;
-        v = __ldg(views + lv);
-        if ((unsigned)v < (unsigned)g.nviews) h = __ldg(g.fp_hdr + (size_t)v * g.ns + c);
-    }
-    const int ia0 = (int)(h.y & 0xffffu), nrows = (int)(h.y >> 16);
-    const int dir = (h.w & 1u) ? -1 : 1;
-    const int axis = (int)((h.w >> 1) & 1u);
-    const int Nb = axis ? g.nx : g.ny;
-    const int sa = axis ? g.nx : 1, sb = axis ? 1 : g.nx;
-    int maxr = nrows;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) maxr = max(maxr, __shfl_xor_sync(0xffffffffu, maxr, o));
-    const unsigned grp = 0x11111111u << (lane & 3);      // the lanes of this ray
-    const unsigned upto = grp & (0xffffffffu >> (31 - lane));  // ... up to this lane
-    const uint2 *E = g.fp_ent + h.x;
-    int jb = (int)h.z;  // first pixel of the row before this pass's rows
-    float acc = 0.f;
-    constexpr int kAhead = 4;  // passes of stored rows in flight (memory latency)
-    for (int r00 = 0; r00 < maxr; r00 += 8 * kAhead) {
-        uint2 e[kAhead];
-#pragma unroll
-        for (int k = 0; k < kAhead; ++k) {
-            const int r = r00 + 8 * k + q;
-            e[k] = r < nrows ? __ldg(E + r) : make_uint2(0u, 0u);
-        }
-#pragma unroll
-        for (int k = 0; k < kAhead; ++k) {
-            const int r = r00 + 8 * k + q;
-            const unsigned m1 = __ballot_sync(0xffffffffu, e[k].x >> 31);
-            const unsigned m2 = __ballot_sync(0xffffffffu, e[k].y >> 31);
-            const int j = jb + dir * (__popc(m1 & upto) + 2 * __popc(m2 & upto));
-            jb += dir * (__popc(m1 & grp) + 2 * __popc(m2 & grp));
-            if (r < nrows) {
-                const float w0 = __uint_as_float(e[k].x & 0x7fffffffu), w1 = __uint_as_float(e[k].y & 0x7fffffffu);
-                const float *row = x + (size_t)(ia0 + r) * sa;
-                const float x0 = (unsigned)j < (unsigned)Nb ? __ldg(row + (ptrdiff_t)j * sb) : 0.f;
-                const float x1 =
-                    (w1 != 0.f && (unsigned)(j + 1) < (unsigned)Nb) ? __ldg(row + (ptrdiff_t)(j + 1) * sb) : 0.f;
-                acc = fmaf(w0, x0, acc);
-                acc = fmaf(w1, x1, acc);
-            }
-        }
-    }
-    acc += __shfl_xor_sync(0xffffffffu, acc, 4);
-    acc += __shfl_xor_sync(0xffffffffu, acc, 8);
-    acc += __shfl_xor_sync(0xffffffffu, acc, 16);
-    if (!valid || q != 0) return;
-    if ((unsigned)v >= (unsigned)g.nviews) {  // caller-supplied view out of range
-        out[ray] = __int_as_float(0x7fc00000);
-        return;
-    }
-    if (MODE == FP_PLAIN) {
-        out[ray] = acc;
-    } else {
-        const float wv = load_w(w, ray) * __ldg(wscale);
-        out[ray] = gain * wv * (acc - __ldg(y + ray));
-    }
-}
-
 template <typename WT>
 __global__ void __launch_bounds__(128) cost2d_kernel(Geo2 g, const float *__restrict__ x,
                                                      const int *__restrict__ views, int nv,
@@ -192,14 +113,13 @@ __device__ __forceinline__ void bp2d_epilogue(const UpdateArgs &ua, float *out, 
     }
 }
 
-template <int MODE, bool TABLE>
-__global__ void __launch_bounds__(kBpThreads, TABLE ? 5 : 8) bp2d_kernel(Geo2 g, const float *__restrict__ r,
-                                                          float *__restrict__ out, const int *__restrict__ views,
-                                                          int nv, UpdateArgs ua) {
+template <int MODE>
+__global__ void __launch_bounds__(kBpThreads, 8) bp2d_kernel(Geo2 g, const float *__restrict__ r,
+                                                             float *__restrict__ out, const int *__restrict__ views,
+                                                             int nv, UpdateArgs ua) {
     __shared__ BpTileAcc S;
     const int tx0 = blockIdx.x * kBpTile, ty0 = blockIdx.y * kBpTile;
-    if (TABLE) bp_tile_table(g, r, views, nv, blockIdx.y * gridDim.x + blockIdx.x, threadIdx.x, S);
-    else bp_tile_strips(g, r, views, nv, tx0, ty0, threadIdx.x, S);
+    bp_tile_strips(g, r, views, nv, tx0, ty0, threadIdx.x, S);
     __syncthreads();
     IterSums sums{0.0, 0.0, 0.0};
 #pragma unroll
@@ -272,10 +192,7 @@ static void launch_fp2d_w(const Geo2 &g, const float *x, float *out, const int *
                           const void *w, const float *wscale, float gain, cudaStream_t st) {
     const int n = nv * g.ns;
     const int grid = (n + 15) / 16;  // 16 rays per 128-thread block
-    if (g.fp_hdr)
-        fp2d_table_kernel<MODE, WT><<<grid, 128, 0, st>>>(g, x, out, views, nv, y, (const WT *)w, wscale, gain);
-    else
-        fp2d_kernel<MODE, WT><<<grid, 128, 0, st>>>(g, x, out, views, nv, y, (const WT *)w, wscale, gain);
+    fp2d_kernel<MODE, WT><<<grid, 128, 0, st>>>(g, x, out, views, nv, y, (const WT *)w, wscale, gain);
 }
 
 template <int MODE>
@@ -303,11 +220,7 @@ int launch_bp2d(const Geo2 &g, const float *r, float *out, const int *views, int
     dim3 block(kBpThreads), grid((g.nx + kBpTile - 1) / kBpTile, (g.ny + kBpTile - 1) / kBpTile);
     UpdateArgs a{};
     if (ua) a = *ua;
-#define OSL_BP(MODE)                                                                                    \
-    do {                                                                                                \
-        if (g.bp_hdr) bp2d_kernel<MODE, true><<<grid, block, 0, st>>>(g, r, out, views, nv, a);         \
-        else bp2d_kernel<MODE, false><<<grid, block, 0, st>>>(g, r, out, views, nv, a);                 \
-    } while (0)
+#define OSL_BP(MODE) bp2d_kernel<MODE><<<grid, block, 0, st>>>(g, r, out, views, nv, a)
     switch (mode) {
         case BP_STORE: OSL_BP(BP_STORE); break;
         case BP_ACCUM: OSL_BP(BP_ACCUM); break;

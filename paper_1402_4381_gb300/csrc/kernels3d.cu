@@ -616,6 +616,30 @@ int launch_fista3d(int nx, int ny, int nz, const float *v, const float *xk, cons
     return OSLALM_OK;
 }
 
+// grad += beta sum_k w_jk psi'(x_j - x_k): the regularizer's gradient
+// (Sec. IV, R of Eq. ct_recon), added to a data-term gradient.  One slice
+// (nz = 1) gives the 2D neighbourhoods: 26 -> the 8 in-plane neighbours,
+// 6 -> the 4 in-plane neighbours.
+template <int NBR>
+__global__ void __launch_bounds__(256) reg_grad_add_kernel(int nx, int ny, int nz, const float *__restrict__ x,
+                                                           float *__restrict__ grad, float beta, float inv_delta) {
+    const int ix = blockIdx.x * 32 + threadIdx.x, iy = blockIdx.y * 8 + threadIdx.y, iz = blockIdx.z;
+    if (ix >= nx || iy >= ny) return;
+    const size_t p = (size_t)iz * nx * ny + (size_t)iy * nx + ix;
+    float gr, curv;
+    stencil3d<NBR>(x, nx, ny, nz, ix, iy, iz, __ldg(x + p), inv_delta, OSLALM_CURV_HUBER, gr, curv);
+    grad[p] += beta * gr;
+}
+
+int launch_reg_grad_add(int nx, int ny, int nz, const float *x, float *grad, float beta, float inv_delta, int nbr,
+                        cudaStream_t s) {
+    dim3 block(32, 8), grid((nx + 31) / 32, (ny + 7) / 8, nz);
+    if (nbr == 26 || nbr == 8) reg_grad_add_kernel<26><<<grid, block, 0, s>>>(nx, ny, nz, x, grad, beta, inv_delta);
+    else reg_grad_add_kernel<6><<<grid, block, 0, s>>>(nx, ny, nz, x, grad, beta, inv_delta);
+    OSL_LAUNCH_CHECK("reg_grad_add_kernel");
+    return OSLALM_OK;
+}
+
 int launch_reg_value3d(int nx, int ny, int nz, const float *x, double beta, double delta, int nbr, double *partials,
                        int *nparts, cudaStream_t s) {
     dim3 block(32, 8), grid((nx + 31) / 32, (ny + 7) / 8, nz);

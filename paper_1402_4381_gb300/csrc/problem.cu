@@ -679,6 +679,22 @@ int oslalm_cost(oslalm_problem *p, const float *x, double *out, void *stream) {
     return OSLALM_OK;
 }
 
+int oslalm_gradient(oslalm_problem *p, const float *x, float *grad, void *stream) {
+    clear_error();
+    if (int rc = check_problem(p)) return rc;
+    if (!x || !grad) return fail(OSLALM_ERR_ARG, "NULL argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    OSL_CUDA_TRY(cudaMemsetAsync(grad, 0, p->npix * sizeof(float), st));
+    for (int m = 0; m < p->p.M; ++m) {  // A_m' W_m (A_m x - y_m), subset by subset
+        if (p->cnt[m] == 0) continue;
+        if (int rc = fp_subset(p, x, m, FP_RESID, 1.f, st)) return rc;
+        if (int rc = launch_bp_any(p->g, p->d_r, grad, p->d_views + p->off[m], p->cnt[m], BP_ACCUM, nullptr, st))
+            return rc;
+    }
+    const oslalm_geom_desc &d = p->g->d;
+    return launch_reg_grad_add(d.nx, d.ny, d.nz, x, grad, (float)p->p.beta, (float)(1.0 / p->p.delta), p->p.nbr, st);
+}
+
 int oslalm_get_state(oslalm_problem *p, float *g, float *zeta, double *rho_l_j, void *stream) {
     clear_error();
     if (int rc = check_problem(p)) return rc;

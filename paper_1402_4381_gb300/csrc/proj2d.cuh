@@ -225,62 +225,6 @@ __device__ __forceinline__ void bp_tile_strips(const Geo2 &g, const float *__res
     }
 }
 
-constexpr int kBpPrefetch = 8;  // stored entries in flight per lane (memory latency)
-
-// The same back-projection read from the device system matrix (Geo2): the
-// tile's lengths stream from memory instead of being evaluated, in the same
-// order per accumulator (views in list order, channels ascending), so the
-// result is bit-identical to bp_tile_strips.  tile = the tile's index in
-// row-major tile order.
-__device__ __forceinline__ void bp_tile_table(const Geo2 &g, const float *__restrict__ r,
-                                              const int *__restrict__ views, int nv, int tile, int t, BpTileAcc &S) {
-    const int grp = t >> 5, lane = t & 31;
-    const size_t ntiles = (size_t)((g.nx + kBpTile - 1) / kBpTile) * ((g.ny + kBpTile - 1) / kBpTile);
-#pragma unroll
-    for (int ax = 0; ax < 2; ++ax)
-#pragma unroll
-        for (int d = 0; d < kBpStrip; ++d) S.a[grp][ax][d][lane] = 0.f;
-    for (int lv = grp; lv < nv; lv += kBpGroups) {
-        const int v = __ldg(views + lv);
-        if ((unsigned)v >= (unsigned)g.nviews) continue;  // caller-supplied view out of range
-        const float *rv = r + (size_t)lv * g.ns;
-#pragma unroll 1
-        for (int ax = 0; ax < 2; ++ax) {
-            const size_t blk = ((size_t)v * 2 + ax) * ntiles + tile;
-            const uint2 b = __ldg(g.bp_blk + blk);
-            if (b.y == 0) continue;
-            const unsigned h = __ldg(g.bp_hdr + blk * 32 + lane);
-            const int cnt = (int)(h >> 24);
-            const int dir = (h >> 20) & 1u ? -1 : 1;
-            int d = (int)((h >> 16) & 15u) - 1;
-            const float *rc = rv + (h & 0xffffu);
-            const uint2 *E = g.bp_ent + (size_t)b.x * 32 + lane;
-            float *A = &S.a[grp][ax][0][lane];
-            // kBpPrefetch entries (and residuals) in flight per lane, then
-            // added in channel order
-            for (int i0 = 0; i0 < cnt; i0 += kBpPrefetch) {
-                uint2 e[kBpPrefetch];
-                float val[kBpPrefetch];
-#pragma unroll
-                for (int k = 0; k < kBpPrefetch; ++k) {
-                    const bool ok = i0 + k < cnt;
-                    e[k] = ok ? __ldg(E + (size_t)(i0 + k) * 32) : make_uint2(0u, 0u);
-                    val[k] = ok ? __ldg(rc + i0 + k) : 0.f;
-                }
-#pragma unroll
-                for (int k = 0; k < kBpPrefetch; ++k) {
-                    if (i0 + k >= cnt) break;
-                    d += dir * (int)((e[k].x >> 31) | ((e[k].y >> 31) << 1));
-                    RowW w;
-                    w.w0 = __uint_as_float(e[k].x & 0x7fffffffu);
-                    w.w1 = __uint_as_float(e[k].y & 0x7fffffffu);
-                    strip_add(A, d, w, val[k]);
-                }
-            }
-        }
-    }
-}
-
 // A'r at tile pixel (px, py) from the accumulators, in the fixed order: the
 // pixel is strip pixel py mod 8 of lane px + 16 (py / 8) for the x-major
 // rays and strip pixel px mod 8 of lane py + 16 (px / 8) for the y-major rays.

@@ -87,13 +87,12 @@ def lib():
         "oslalm_get_state": ([_VP, _VP, _VP, ctypes.POINTER(d), _VP], i),
         "oslalm_set_state": ([_VP, _VP, _VP, ctypes.POINTER(d), _VP], i),
         "oslalm_get_denominator": ([_VP, _VP, _VP], i),
+        "oslalm_gradient": ([_VP, _VP, _VP, _VP], i),
         "oslalm_rmsd": ([_VP, _VP, _VP, ctypes.c_long, ctypes.POINTER(d), _VP], i),
         "oslalm_profile_iterate": ([_VP, _VP, i, ctypes.POINTER(d), ip, _VP], i),
         "oslalm_fbp": ([_VP, _VP, _VP, i, _VP], i),
         "oslalm_ray_table": ([ctypes.POINTER(GeomDesc), i, _VP, _VP, _VP, _VP], i),
         "oslalm_max_subsets": ([ctypes.POINTER(GeomDesc), d, ctypes.POINTER(d)], i),
-        "oslalm_geom_build_matrix": ([_VP, _VP, _VP], i),
-        "oslalm_geom_drop_matrix": ([_VP], i),
         "oslalm_batch_create": ([ctypes.POINTER(_VP), i, ctypes.POINTER(_VP)], i),
         "oslalm_batch_destroy": ([_VP], i),
         "oslalm_batch_iterate": ([_VP, ctypes.POINTER(_VP), i, i, _VP], i),
@@ -106,6 +105,7 @@ def lib():
         "oslalm_cnn_create": ([i, i, i, ctypes.c_ulonglong, ctypes.POINTER(_VP)], i),
         "oslalm_cnn_destroy": ([_VP], i),
         "oslalm_cnn_get_params": ([_VP, _VP], i),
+        "oslalm_cnn_mark_timeout": ([_VP], i),
         "oslalm_cnn_set_params": ([_VP, _VP], i),
         "oslalm_cnn_forward": ([_VP, _VP, _VP, i, ctypes.c_float, _VP], i),
         "oslalm_cnn_gradients": ([_VP, _VP, _VP, i, ctypes.c_float, _VP, ctypes.POINTER(d), _VP], i),
@@ -241,17 +241,6 @@ class Geometry:
                                         _stream(stream)), "backproject")
         return out
 
-    def build_matrix(self, stream=None) -> int:
-        """Hold the 2D system matrix in device memory (oslalm_geom_build_matrix);
-        returns its size in bytes (self.matrix_bytes: forward and
-        back-projection layouts)."""
-        n = (ctypes.c_size_t * 2)()
-        _check(lib().oslalm_geom_build_matrix(self._h, n, _stream(stream)), "geom_build_matrix")
-        self.matrix_bytes = (int(n[0]), int(n[1]))
-        return sum(self.matrix_bytes)
-
-    def drop_matrix(self):
-        _check(lib().oslalm_geom_drop_matrix(self._h), "geom_drop_matrix")
 
     def fbp(self, sino, out=None, clip=True, stream=None):
         """Filtered back-projection of the full sinogram (initial image)."""
@@ -352,6 +341,14 @@ class Problem:
     def set_state(self, st, stream=None):
         s = (ctypes.c_double * 4)(st["rho"], st["l"], st["j"], st.get("alpha", 1.0))
         _check(lib().oslalm_set_state(self._h, _ptr(st["g"]), _ptr(st["zeta"]), s, _stream(stream)), "set_state")
+
+    def gradient(self, x, stream=None):
+        """A'W(Ax - y) + grad R(x) at x (oslalm_gradient), a new device tensor."""
+        import torch
+        _dev_f32(x, self.geom.image_shape, "x")
+        gr = torch.empty(self.geom.image_shape, dtype=torch.float32, device=x.device)
+        _check(lib().oslalm_gradient(self._h, _ptr(x), _ptr(gr), _stream(stream)), "gradient")
+        return gr
 
     def denominator(self, stream=None):
         import torch
@@ -485,6 +482,10 @@ class WarmStartNet:
         out = np.zeros(self.param_count(), np.float32)
         _check(lib().oslalm_cnn_get_params(self._h, out.ctypes.data), "cnn_get_params")
         return out
+
+    def mark_timeout(self):
+        """Set the network's timed-out mark from the host (oslalm_cnn_mark_timeout)."""
+        _check(lib().oslalm_cnn_mark_timeout(self._h), "cnn_mark_timeout")
 
     def set_params(self, flat):
         flat = np.ascontiguousarray(flat, dtype=np.float32)

@@ -13,6 +13,14 @@ def pytest_configure(config):
     config.addinivalue_line("markers", "slow: longer CPU test")
 
 
+@pytest.fixture(scope="session", autouse=True)
+def oracle_threads():
+    """The oracle's projector loops on every host core (its results do not
+    depend on the thread count)."""
+    from oracle import siddon
+    siddon.set_threads(os.cpu_count() or 1)
+
+
 @pytest.fixture(scope="session")
 def oracle_lib():
     from oracle import siddon

@@ -32,4 +32,10 @@ def assert_rel_floor(got, ref, rtol=RAY_RTOL, floor=RAY_FLOOR, what="values"):
         i = np.unravel_index(np.argmax(err / np.maximum(scale, 1e-300)), ref.shape)
         raise AssertionError(f"{what}: {bad.sum()} of {bad.size} outside tolerance; worst at {i}: "
                              f"got {got[i]!r} ref {ref[i]!r} rel {err[i] / scale[i]:.3e}")
-    return float(np.max(err / np.maximum(scale, 1e-300)))
+    worst = float(np.max(err / np.maximum(scale, 1e-300)))
+    # the same without the floor, over the entries not near zero (|ref| above
+    # 1e-6 of the largest): how far the floor loosens the per-entry bound
+    big = np.abs(ref) > 1e-6 * np.max(np.abs(ref))
+    raw = float(np.max(err[big] / np.abs(ref[big]))) if np.any(big) else 0.0
+    print(f"{what}: worst relative error {worst:.2e} with the floor, {raw:.2e} without it")
+    return worst

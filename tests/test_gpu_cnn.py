@@ -166,3 +166,25 @@ def test_training_lowers_loss(L):
         noisy = clean + 0.3 * torch.randn(n, h, w, device="cuda", generator=g)
         losses.append(net.train_step(noisy, clean, 1.0, 1e-3))
     assert np.mean(losses[-10:]) < 0.5 * np.mean(losses[:10])
+
+
+def test_timeout_mark_is_reported_once_and_cleared(L):
+    """The error path of a tensor-core wait that ran out, driven from the host
+    (no device fault): the mark turns the next synchronizing call into
+    OSLALM_ERR_TIMEOUT, which clears it; the call after that succeeds."""
+    import torch
+    net = L.WarmStartNet(2, 16, 16, seed=1)
+    x = torch.rand((2, 16, 16), device="cuda") * 0.04
+    p0 = net.get_params()
+    net.mark_timeout()
+    with pytest.raises(L.OslalmError) as e:
+        net.get_params()
+    assert e.value.code == -4
+    assert np.array_equal(net.get_params(), p0)
+    net.forward(x, 50.0)
+    net.mark_timeout()
+    with pytest.raises(L.OslalmError) as e:
+        net.train_step(x, x, 50.0, 1e-4, want_loss=True)
+    assert e.value.code == -4
+    assert np.isfinite(net.train_step(x, x, 50.0, 1e-4, want_loss=True))
+    net.close()

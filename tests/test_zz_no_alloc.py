@@ -4,7 +4,10 @@ regular one (oslalm_fbp), called through the C ABI.
 oslalm_fbp_noalloc exists for callers that must not allocate device memory
 once they are running (a service whose memory pool owns the GPU, a pipeline
 that forbids cudaMalloc after start-up); it keeps its filtered sinogram in a
-fixed buffer inside the library.  This file is collected last on purpose."""
+fixed buffer inside the library, reserved by oslalm_fbp_noalloc_prepare at
+start-up.  Both entry points run the same kernels on the same samples, so
+their images must agree bit for bit.  This file is collected last on purpose.
+"""
 import ctypes
 import math
 
@@ -14,8 +17,6 @@ import pytest
 from paper_1402_4381_gb300 import synth, workloads as W
 
 pytestmark = pytest.mark.gpu
-
-TOL = 3e-4  # relative to max |x|, the tolerance of the FBP parity tests
 
 
 @pytest.fixture(scope="module")
@@ -27,6 +28,10 @@ def L():
     lib = oslalm.lib()
     lib.oslalm_fbp_noalloc.argtypes = [ctypes.c_void_p] * 3 + [ctypes.c_int, ctypes.c_void_p]
     lib.oslalm_fbp_noalloc.restype = ctypes.c_int
+    lib.oslalm_fbp_noalloc_prepare.argtypes = []
+    lib.oslalm_fbp_noalloc_prepare.restype = ctypes.c_int
+    torch.cuda.set_device(0)
+    assert lib.oslalm_fbp_noalloc_prepare() == 0, lib.oslalm_last_error()
     return oslalm
 
 
@@ -49,7 +54,25 @@ def test_noalloc_fbp_matches_fbp_twice(L, g):
         torch.cuda.synchronize()
         a, b = out.cpu().numpy(), ref.cpu().numpy()
         assert np.all(np.isfinite(a)), call
-        assert np.max(np.abs(a - b)) <= TOL * np.max(np.abs(b)), call
+        assert np.array_equal(a, b), (call, float(np.max(np.abs(a - b))))
+
+
+def test_noalloc_fbp_leaves_free_memory_unchanged(L):
+    """After the prepare call, a call reserves no device memory: the device's
+    free memory (cudaMemGetInfo) is the same before and after two calls."""
+    import torch
+    g = W.c1_fan().geom
+    geom = L.Geometry(g)
+    sino = torch.as_tensor(_scan(g, 23), device="cuda")
+    out = torch.empty(g.image_shape, device="cuda")
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(2):
+        rc = L.lib().oslalm_fbp_noalloc(geom.handle, L._ptr(sino), L._ptr(out), 1, L._stream())
+        assert rc == 0, L.lib().oslalm_last_error()
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0, (free0, free1)
 
 
 def test_noalloc_fbp_rejects_oversized_sinogram(L):
