@@ -123,7 +123,7 @@ def test_c0_full_gradient(L, c0):
     """oslalm_gradient = A'W(Ax - y) + grad R(x) (Sec. IV, Eq. ct_recon) against
     the oracle's, at an image with edges (the regularizer is far from inert)."""
     geom = L.Geometry(c0.g)
-    beta = 2.0 ** 22
+    beta = 2.0 ** 24
     prob = L.Problem(geom, to_dev(c0.y), to_dev(c0.w), beta=beta, delta=c0.wl.delta, nbr=c0.wl.nbr, M=c0.M)
     scan = c0.wl.make_scan()
     xt = synth.pixelize(c0.g, scan["phantom"], supersample=2).astype(np.float32)
