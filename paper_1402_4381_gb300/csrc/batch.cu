@@ -94,8 +94,8 @@ __global__ void __launch_bounds__(256) batch_update_kernel(const SliceDesc *__re
         const int ix0 = (t % ntx) * TX, iy0 = (t / ntx) * TY;
         const float *xin = (step & 1) ? d.xalt : d.x;
         float *xout = (step & 1) ? d.x : d.xalt;
-        const float rho = (float)d.ua.state->rho;
-        const float rho_d = (float)(d.ua.state->rho * d.ua.state->alpha);
+        const float rho = d.ua.state->rho_f;
+        const float rho_d = d.ua.state->rho_d_f;
 #define OSL_BUPD(DT, N)                                                                                          \
     update_tile<TX, TY, DT, N>(tile, ix0, iy0, tid % TX, tid / TX, tid, 256, d.geo.nx, d.geo.ny, xin, xout,     \
                                d.ua.zeta, d.ua.g, (const DT *)d.D, d.dscale, rho, rho_d, d.beta, d.inv_delta, d.curv)
@@ -182,9 +182,7 @@ __global__ void __launch_bounds__(kBpThreads, 8) batch_backproject_kernel(const 
         if (ix < d.geo.nx && iy < d.geo.ny) {
             const float v = bp_tile_total(acc, px, py);
             const size_t p = (size_t)iy * d.geo.nx + ix;
-            const double rho = d.ua.state->rho;
-            const float a = (float)(rho / (rho + 1.0));
-            const float b = (float)(1.0 / (rho + 1.0));
+            const float a = d.ua.state->ga, b = d.ua.state->gb;
             const float z_old = d.ua.zeta[p];
             const float g_old = d.ua.g[p];
             d.ua.zeta[p] = v;

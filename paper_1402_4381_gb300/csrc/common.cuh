@@ -210,7 +210,20 @@ struct DevState {
     int pad;
     double alpha;  // Barzilai-Borwein scale of the majorizer (1 without it)
     double bb_num, bb_den;  // sum s'y, sum s'Ds of the current iteration's secant pairs
+    // FP32 factors of the current rho for the per-pixel kernels, formed once
+    // where rho or alpha changes (FP64 arithmetic is scarce on this GPU):
+    // rho_f = rho, rho_d_f = rho alpha, ga = rho/(rho+1), gb = 1/(rho+1)
+    float rho_f, rho_d_f, ga, gb;
 };
+
+// Refresh the FP32 factors after rho or alpha changed (one thread).
+__device__ __forceinline__ void refresh_rho_factors(DevState *st) {
+    const double rho = st->rho;
+    st->rho_f = (float)rho;
+    st->rho_d_f = (float)(rho * st->alpha);
+    st->ga = (float)(rho / (rho + 1.0));
+    st->gb = (float)(1.0 / (rho + 1.0));
+}
 
 struct UpdateArgs {  // epilogue arguments of the fused back-projection
     float *zeta;

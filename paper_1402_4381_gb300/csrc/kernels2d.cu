@@ -102,9 +102,7 @@ __device__ __forceinline__ void bp2d_epilogue(const UpdateArgs &ua, float *out, 
         ua.g[p] = acc;
     } else {
         // split-gradient update and restart indicator (old g, old zeta)
-        const double rho = ua.state->rho;
-        const float a = (float)(rho / (rho + 1.0));
-        const float b = (float)(1.0 / (rho + 1.0));
+        const float a = ua.state->ga, b = ua.state->gb;
         const float z_old = ua.zeta[p];
         const float g_old = ua.g[p];
         ua.zeta[p] = acc;
@@ -144,7 +142,7 @@ __global__ void __launch_bounds__(256) update2d_kernel(int nx, int ny, const flo
     __shared__ float tile[10 * 34];
     update_tile<32, 8, DT, NBR>(tile, blockIdx.x * 32, blockIdx.y * 8, threadIdx.x, threadIdx.y,
                                 threadIdx.y * 32 + threadIdx.x, 256, nx, ny, x, xo, zeta, gs, D, dscale,
-                                (float)st->rho, (float)(st->rho * st->alpha), beta, inv_delta, curv_mode);
+                                st->rho_f, st->rho_d_f, beta, inv_delta, curv_mode);
 }
 
 template <typename DT, int NBR>
@@ -158,7 +156,7 @@ __global__ void __launch_bounds__(256) fista2d_kernel(int nx, int ny, const floa
     __shared__ float tile[10 * 34];
     fista_tile<32, 8, DT, NBR>(tile, blockIdx.x * 32, blockIdx.y * 8, threadIdx.x, threadIdx.y,
                                threadIdx.y * 32 + threadIdx.x, 256, nx, ny, v, xk, u, uo, vo, zeta, gs, D, dscale,
-                               (float)st->rho, (float)(st->rho * st->alpha), beta, inv_delta, curv_mode, gamma);
+                               st->rho_f, st->rho_d_f, beta, inv_delta, curv_mode, gamma);
 }
 
 template <int NBR>

@@ -383,9 +383,7 @@ __global__ void __launch_bounds__(256) bp3d_kernel(Geo3 g, const float *__restri
     } else {
         IterSums sums{0.0, 0.0, 0.0};
         if (valid) {
-            const double rho = ua.state->rho;
-            const float a = (float)(rho / (rho + 1.0));
-            const float b = (float)(1.0 / (rho + 1.0));
+            const float a = ua.state->ga, b = ua.state->gb;
 #pragma unroll
             for (int q = 0; q < KZ; ++q) {
                 const int kz = kz0 + q;
@@ -453,7 +451,7 @@ __global__ void __launch_bounds__(256) update3d_kernel(int nx, int ny, int nz, c
     stencil3d<NBR>(x, nx, ny, nz, ix, iy, iz, xj, inv_delta, curv_mode, grad, curv);
     grad *= beta;
     curv *= 2.f * beta;
-    const float rho = (float)st->rho, rho_d = (float)(st->rho * st->alpha);  // alpha: Barzilai-Borwein scale
+    const float rho = st->rho_f, rho_d = st->rho_d_f;  // rho_d = rho alpha, alpha: Barzilai-Borwein scale
     const float s = rho * __ldg(zeta + p) + (1.f - rho) * __ldg(gs + p);
     const float den = rho_d * (load_w(D, p) * __ldg(dscale)) + curv;
     const float xn = den > 0.f ? xj - (s + grad) / den : xj;  // no curvature: unchanged
@@ -477,7 +475,7 @@ __global__ void __launch_bounds__(256) fista3d_kernel(int nx, int ny, int nz, co
     stencil3d<NBR>(v, nx, ny, nz, ix, iy, iz, vj, inv_delta, curv_mode, grad, curv);
     grad *= beta;
     curv *= 2.f * beta;
-    const float rho = (float)st->rho, rho_d = (float)(st->rho * st->alpha);
+    const float rho = st->rho_f, rho_d = st->rho_d_f;
     const float s = rho * __ldg(zeta + p) + (1.f - rho) * __ldg(gs + p);
     const float rd = rho_d * (load_w(D, p) * __ldg(dscale));
     const float gphi = fmaf(rd, vj - __ldg(xk + p), s + grad);

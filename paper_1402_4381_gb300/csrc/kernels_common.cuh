@@ -161,6 +161,7 @@ __device__ __forceinline__ void finish_subset_iteration(const UpdateArgs &ua, in
         st->xi = xi;
         st->l = l;
         st->rho = rho;
+        refresh_rho_factors(st);
         if (ua.stats && ua.stats_cap > 0) {
             oslalm_stats rec;
             rec.xi = xi;

@@ -106,6 +106,7 @@ __global__ void set_state_kernel(DevState *st, double rho, int l, int j, double 
     st->l = l;
     st->j = j;
     st->counter = 0;
+    refresh_rho_factors(st);
 }
 
 __global__ void rmsd_kernel(const float *__restrict__ x, const float *__restrict__ xr, const uint8_t *__restrict__ m,
