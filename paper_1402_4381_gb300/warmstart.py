@@ -41,7 +41,8 @@ from . import roi, synth, workloads as W
 SCALE = 1.0 / synth.MU_WATER  # network units: water = 1
 HU = synth.HU
 THRESHOLDS = (20.0, 10.0, 5.0, 2.0, 1.0)
-FULL_REF_SCHEDULE = ((24, 60), (8, 60), (2, 100), (1, 800))
+FULL_REF_SCHEDULE = ((24, 100), (8, 100), (2, 200), (1, 2000))
+ROUTE_SCHEDULE = ((24, 100), (8, 100), (2, 300))  # the subset-reduction route that reaches 1 HU
 
 
 def base_workload(nx=512, nviews=984, ns=888, M=24) -> W.Workload:
@@ -77,30 +78,43 @@ def make_scans(wls, workers=None):
         return list(ex.map(_scan, wls, chunksize=4))
 
 
-def _problem(oslalm, torch, geomh, wl, y, w, M=None, use_graph=True):
+def _problem(oslalm, torch, geomh, wl, y, w, M=None, use_graph=True, storage=None):
     dev = torch.device("cuda", torch.cuda.current_device())
+    wd, dd = storage or (wl.w_dtype, wl.d_dtype)
     return oslalm.Problem(geomh, torch.as_tensor(y, device=dev), torch.as_tensor(w, device=dev), beta=wl.beta,
-                          delta=wl.delta, nbr=wl.nbr, M=M or wl.M, w_dtype=wl.w_dtype, d_dtype=wl.d_dtype,
-                          use_graph=use_graph)
+                          delta=wl.delta, nbr=wl.nbr, M=M or wl.M, w_dtype=wd, d_dtype=dd, use_graph=use_graph)
 
 
-def run_batched(oslalm, torch, geomh, wls, scans, xs, schedule, chunk=64):
+def run_batched(oslalm, torch, geomh, wls, scans, xs, schedule, chunk=64, storage=None, last_change=None):
     """Advance the images xs (in place) through `schedule` = ((M, iters), ...)
     with the batched persistent path, `chunk` scans per batch; a new M
-    restarts the method (init) from the current image."""
+    restarts the method (init) from the current image.  last_change (a mask,
+    or None): also return, per scan, the RMS difference (HU) made by the
+    last quarter of the final stage."""
+    changes = []
     for k in range(0, len(wls), chunk):
-        for M, iters in schedule:
-            probs = [_problem(oslalm, torch, geomh, wl, y, w, M=M, use_graph=False)
+        for si, (M, iters) in enumerate(schedule):
+            probs = [_problem(oslalm, torch, geomh, wl, y, w, M=M, use_graph=False, storage=storage)
                      for wl, (y, w) in zip(wls[k:k + chunk], scans[k:k + chunk])]
             for p, x in zip(probs, xs[k:k + chunk]):
                 p.init(x)
             b = oslalm.Batch(probs)
-            b.iterate(xs[k:k + chunk], iters, use_graph=True)
+            if last_change is not None and si == len(schedule) - 1:
+                q = iters // 4
+                b.iterate(xs[k:k + chunk], iters - q, use_graph=True)
+                before = [x.clone() for x in xs[k:k + chunk]]
+                b.iterate(xs[k:k + chunk], q, use_graph=True)
+                torch.cuda.synchronize()
+                m = torch.as_tensor(last_change.astype(np.uint8), device=before[0].device)
+                changes += [oslalm.rmsd(x, x_b, m) / HU for x, x_b in zip(xs[k:k + chunk], before)]
+                del before
+            else:
+                b.iterate(xs[k:k + chunk], iters, use_graph=True)
             torch.cuda.synchronize()
             b.close()
             for p in probs:
                 p.close()
-    return xs
+    return (xs, changes) if last_change is not None else xs
 
 
 def train(torch, net, xs, ts, epochs, lr, batch, seed=0, log=None):
@@ -170,6 +184,70 @@ def evaluate(oslalm, torch, geomh, wls, scans, x0s, xstars, mask_np, init_fn=Non
     return rows
 
 
+def evaluate_route(oslalm, torch, geomh, wls, scans, x0s, xstars, mask_np, init_fn=None,
+                   schedule=ROUTE_SCHEDULE, thresholds=THRESHOLDS, stop_hu=1.0):
+    """Per scan: the subset-reduction route (OS-LALM with `schedule` =
+    ((M, iterations), ...), each stage restarting the method from the
+    current image; FP32 storage) from x0 (or init_fn(x0)), until the RMS
+    difference to x* falls to stop_hu.  Timed with CUDA events: network
+    inference, every stage's oslalm_init (D recomputed) and the iterations;
+    the RMS differences after every iteration are not timed."""
+    dev = x0s[0].device
+    mask = torch.as_tensor(mask_np.astype(np.uint8), device=dev)
+    stream = torch.cuda.current_stream()
+    if init_fn is not None:
+        init_fn(x0s[0])
+        torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn):
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        e1.synchronize()
+        return out, e0.elapsed_time(e1)
+
+    rows = []
+    for wl, (y, w), x0, xs in zip(wls, scans, x0s, xstars):
+        torch.cuda.synchronize()
+        x, t = timed(lambda: init_fn(x0) if init_fn else x0.clone())
+        curve = [oslalm.rmsd(x, xs, mask) / HU]
+        reached = {th: (0, t / 1000.0) for th in thresholds if curve[0] <= th}
+        k, done = 0, curve[0] <= stop_hu
+        for M, n in schedule:
+            if done:
+                break
+            p = _problem(oslalm, torch, geomh, wl, y, w, M=M, storage=("f32", "f32"))
+            t += timed(lambda: p.init(x))[1]
+            for _ in range(n):
+                t += timed(lambda: p.iterate(x, 1))[1]
+                k += 1
+                r = oslalm.rmsd(x, xs, mask) / HU
+                curve.append(r)
+                for th in thresholds:
+                    if th not in reached and r <= th:
+                        reached[th] = (k, t / 1000.0)
+                if r <= stop_hu:
+                    done = True
+                    break
+            p.close()
+        rows.append(dict(curve=curve, reached=reached))
+    return rows
+
+
+def summarize_route(rows, thresholds=THRESHOLDS):
+    out = {"thresholds": {}}
+    for th in thresholds:
+        hit = [r["reached"][th] for r in rows if th in r["reached"]]
+        out["thresholds"][f"{th:g}"] = {
+            "reached": len(hit), "of": len(rows),
+            "mean_iterations": float(np.mean([h[0] for h in hit])) if hit else None,
+            "mean_seconds": float(np.mean([h[1] for h in hit])) if hit else None,
+            "median_seconds": float(np.median([h[1] for h in hit])) if hit else None,
+        }
+    return out
+
+
 def summarize(rows, thresholds=THRESHOLDS):
     curves = np.array([r["curve"] for r in rows])
     out = {"rmsd_hu_mean_by_iteration": [round(float(v), 3) for v in curves.mean(axis=0)], "thresholds": {}}
@@ -236,21 +314,34 @@ def experiment(n_train=2000, n_test=100, target_iters=200, epochs=30, batch=8, l
     def cnn_init(x0):
         return torch.clamp(inf.forward(x0.view(1, g.ny, g.nx), SCALE), min=0.0).view(x0.shape)
 
-    t0 = time.time()
-    xstars = run_batched(oslalm, torch, geomh, wls_te, scans_te, [x.clone() for x in x0_te], ref_schedule, chunk)
-    t_ref = time.time() - t0
-    log(f"references: {t_ref:.1f} s")
     mask = roi.roi_mask(g)
+    t0 = time.time()
+    xstars, ref_change = run_batched(oslalm, torch, geomh, wls_te, scans_te, [x.clone() for x in x0_te], ref_schedule,
+                                     chunk, storage=("f32", "f32"), last_change=mask)
+    t_ref = time.time() - t0
+    log(f"references: {t_ref:.1f} s; change over the last quarter of the final stage: max "
+        f"{max(ref_change):.4f} HU")
     fbp_rows = evaluate(oslalm, torch, geomh, wls_te, scans_te, x0_te, xstars, mask, None, n_eval_iter)
     cnn_rows = evaluate(oslalm, torch, geomh, wls_te, scans_te, x0_te, xstars, mask, cnn_init, n_eval_iter)
+    t0 = time.time()
+    fbp_route = evaluate_route(oslalm, torch, geomh, wls_te, scans_te, x0_te, xstars, mask, None)
+    cnn_route = evaluate_route(oslalm, torch, geomh, wls_te, scans_te, x0_te, xstars, mask, cnn_init)
+    log(f"route evaluation: {time.time() - t0:.1f} s")
     return {
         "geometry": {"image": [g.ny, g.nx], "views": g.nviews, "channels": g.ns, "M": M},
         "train": {"scans": n_train, "target_iterations": target_iters, "epochs": epochs, "batch": batch,
                   "steps": steps, "seconds": round(t_train, 2), "tflops_bf16": round(flops / t_train / 1e12, 2),
                   "loss_by_epoch": [round(v, 6) for v in hist]},
         "held_out": n_test, "reference_schedule": [list(s) for s in ref_schedule],
-        "fbp_init": summarize(fbp_rows), "cnn_init": summarize(cnn_rows),
-        "paired": paired_gain(fbp_rows, cnn_rows),
+        "reference_storage": "f32",
+        "reference_last_quarter_change_hu": {"max": round(max(ref_change), 5),
+                                             "mean": round(float(np.mean(ref_change)), 5)},
+        "configured": {"M": M, "iterations": n_eval_iter, "storage": [base.w_dtype, base.d_dtype],
+                       "fbp_init": summarize(fbp_rows), "cnn_init": summarize(cnn_rows),
+                       "paired": paired_gain(fbp_rows, cnn_rows)},
+        "route": {"schedule": [list(s) for s in ROUTE_SCHEDULE], "stop_hu": 1.0, "storage": "f32",
+                  "fbp_init": summarize_route(fbp_route), "cnn_init": summarize_route(cnn_route),
+                  "paired": paired_gain(fbp_route, cnn_route)},
         "seconds": {"scan_generation_cpu": round(t_scan, 1), "targets_gpu": round(t_targets, 1),
                     "references_gpu": round(t_ref, 1)},
     }
