@@ -216,6 +216,13 @@ static int validate(const oslalm_geom_desc *d) {
                 return fail(OSLALM_ERR_ARG, "cone beam: offset_t must be a multiple of 1/2 row");
             if (d->nt > 256) return fail(OSLALM_ERR_RANGE, "cone beam: at most 256 detector rows");
             if (d->nz > 4096) return fail(OSLALM_ERR_RANGE, "cone beam: at most 4096 slices");
+            // a ray rises by less than one slice per transaxial row (so a row
+            // meets at most two slices): tan(cone angle) <= (nt/2 + |offset_t|)
+            // dt / dsd, and a row is at most sqrt(2) max(dx, dy) long in the plane
+            const double tan_cone = (0.5 * d->nt + fabs(d->offset_t)) * d->dt / d->dsd;
+            if (tan_cone * sqrt(2.0) * fmax(d->dx, d->dy) >= d->dz)
+                return fail(OSLALM_ERR_RANGE, "cone beam: cone angle too wide for the slice thickness (a ray "
+                                              "must rise by less than one slice per pixel row)");
         }
         double gmax = fabs((0.5 * d->ns + fabs(d->offset_s)) * d->ds / d->dsd);
         if (d->kind == OSLALM_FAN2D_ARC && gmax >= 1.2)

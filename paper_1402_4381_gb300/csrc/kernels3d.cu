@@ -103,6 +103,7 @@ __device__ __forceinline__ float span_tau(const DSpan &s, bool inc, float v, flo
 }
 
 // fraction interval of the row in which the coordinate lies in cell kk
+// (the general form, for any cell)
 __device__ __forceinline__ void dcell_frac(const DSpan &s, bool inc, float kk, float &flo, float &fhi) {
     const float jl = floorf(s.lo), jh = floorf(s.hi);
     if (jl == jh) {
@@ -120,6 +121,52 @@ __device__ __forceinline__ void dcell_frac(const DSpan &s, bool inc, float kk, f
     const float t_hi = kk + 1.f < s.hi ? span_tau(s, inc, kk + 1.f, rw) : (inc ? 1.f : 0.f);
     flo = fmaxf(fminf(t_lo, t_hi), 0.f);
     fhi = fminf(fmaxf(t_lo, t_hi), 1.f);
+}
+
+// The same fraction intervals for the (at most two) cells of a span, with
+// the one crossing evaluated once: a span is narrower than a cell, so it
+// covers jl = floor(lo) and, when it crosses jl + 1, also jl + 1.  rw =
+// rcp_approx(2 hw) of the span (a per-ray constant).  cell(0) / cell(1)
+// give exactly what dcell_frac gives for cells jl / jl + 1.
+struct SpanCells {
+    float jl;      // first cell (relative to the span's base)
+    bool two;      // floor(hi) > jl
+    bool inc;
+    bool cross;    // jl + 1 < hi: the second cell is entered
+    float tau;     // fraction at which the coordinate passes jl + 1
+    __device__ __forceinline__ void cell(int which, float &flo, float &fhi) const {
+        const float e_lo = inc ? 0.f : 1.f, e_hi = inc ? 1.f : 0.f;
+        if (!two) {
+            flo = which == 0 ? 0.f : 1.f;
+            fhi = which == 0 ? 1.f : 0.f;
+            return;
+        }
+        float t_lo, t_hi;
+        if (which == 0) {
+            t_lo = e_lo;
+            t_hi = cross ? tau : e_hi;
+        } else {
+            if (!cross) {
+                flo = 1.f;
+                fhi = 0.f;
+                return;
+            }
+            t_lo = tau;
+            t_hi = e_hi;
+        }
+        flo = fmaxf(fminf(t_lo, t_hi), 0.f);
+        fhi = fminf(fmaxf(t_lo, t_hi), 1.f);
+    }
+};
+
+__device__ __forceinline__ SpanCells span_cells(const DSpan &s, bool inc, float rw) {
+    SpanCells o;
+    o.jl = floorf(s.lo);
+    o.two = floorf(s.hi) != o.jl;
+    o.inc = inc;
+    o.cross = __fadd_rn(o.jl, 1.f) < s.hi;
+    o.tau = o.two && o.cross ? span_tau(s, inc, __fadd_rn(o.jl, 1.f), rw) : 0.f;
+    return o;
 }
 
 // transaxial span of row ia, compensated like the height span: the centre
@@ -205,29 +252,37 @@ __device__ __forceinline__ ACC march3(const Geo3 &g, const Ray3 &rp, int u, cons
     int ia0, ia1;
     ray_rows3(g, rp, z, ia0, ia1);
     const bool binc = b_increasing(rp), zinc = z.inc;
+    // per-ray reciprocals of the two span widths (the spans' half-widths are
+    // the same in every row)
+    const float rwb = rcp_approx(__fadd_rn(bspan(rp, 0).hw, bspan(rp, 0).hw));
+    const float rwz = rcp_approx(__fadd_rn(z.hwz, z.hwz));
     ACC acc = 0;
     for (int ia = ia0; ia <= ia1; ++ia) {
         const DSpan sb_ = bspan(rp, ia);
         const DSpan sz_ = zspan(rp, z, ia);
-        const float jlo = floorf(sb_.lo), jhi = floorf(sb_.hi);
-        const float klo = floorf(sz_.lo), khi = floorf(sz_.hi);
-        if (jlo == jhi && klo == khi) {  // the row stays inside one voxel
-            const int j = sb_.base + (int)jlo, kz = sz_.base + (int)klo;
+        const SpanCells cb = span_cells(sb_, binc, rwb);
+        const SpanCells cz = span_cells(sz_, zinc, rwz);
+        if (!cb.two && !cz.two) {  // the row stays inside one voxel
+            const int j = sb_.base + (int)cb.jl, kz = sz_.base + (int)cz.jl;
             if ((unsigned)j < (unsigned)Nb && (unsigned)kz < (unsigned)g.nz)
                 acc += (ACC)z.L * (ACC)__ldg(x + (size_t)ia * sa + (size_t)j * sb + (size_t)kz * sz);
             continue;
         }
-        for (float jj = jlo; jj <= jhi; jj += 1.f) {
-            const int j = sb_.base + (int)jj;
+#pragma unroll
+        for (int bj = 0; bj < 2; ++bj) {
+            if (bj == 1 && !cb.two) break;
+            const int j = sb_.base + (int)cb.jl + bj;
             if ((unsigned)j >= (unsigned)Nb) continue;
             float blo, bhi;
-            dcell_frac(sb_, binc, jj, blo, bhi);
+            cb.cell(bj, blo, bhi);
             if (!(bhi > blo)) continue;
-            for (float kk = klo; kk <= khi; kk += 1.f) {
-                const int kz = sz_.base + (int)kk;
+#pragma unroll
+            for (int bk = 0; bk < 2; ++bk) {
+                if (bk == 1 && !cz.two) break;
+                const int kz = sz_.base + (int)cz.jl + bk;
                 if ((unsigned)kz >= (unsigned)g.nz) continue;
                 float zlo_, zhi_;
-                dcell_frac(sz_, zinc, kk, zlo_, zhi_);
+                cz.cell(bk, zlo_, zhi_);
                 const float ch = pair_len(blo, bhi, zlo_, zhi_, z.L);
                 if (ch > 0.f) acc += (ACC)ch * (ACC)__ldg(x + (size_t)ia * sa + (size_t)j * sb + (size_t)kz * sz);
             }
@@ -313,6 +368,7 @@ __global__ void __launch_bounds__(256) bp3d_kernel(Geo3 g, const float *__restri
             const int v = __ldg(views + lv);
             if ((unsigned)v >= (unsigned)g.nviews) continue;
             const View2 vw = g.views[v];
+            const Ray3 *rr = g.rays + (size_t)v * g.ns;
             const float U = px * vw.cu + py * vw.su + g.dso;
             const float Bq = -px * vw.su + py * vw.cu;
             // flat-detector channel window of the pixel's circumscribed disk
@@ -322,7 +378,6 @@ __global__ void __launch_bounds__(256) bp3d_kernel(Geo3 g, const float *__restri
             const float shi = g.dsd * (T + td) / fmaxf(1.f - T * td, 1e-6f);
             const int c0i = max(0, (int)ceilf(slo * g.inv_ds + g.c0 - 0.02f));
             const int c1i = min(g.ns - 1, (int)floorf(shi * g.inv_ds + g.c0 + 0.02f));
-            const Ray3 *rr = g.rays + (size_t)v * g.ns;
             const float *rv = r + (size_t)lv * g.nt * g.ns;
             for (int c = c0i; c <= c1i; ++c) {
                 const Ray3 rp = rr[c];
@@ -330,8 +385,11 @@ __global__ void __launch_bounds__(256) bp3d_kernel(Geo3 g, const float *__restri
                 const int ia = axis ? iy : ix;
                 const int jb = axis ? ix : iy;
                 const DSpan sb_ = bspan(rp, ia);
+                const SpanCells cb = span_cells(sb_, b_increasing(rp), rcp_approx(__fadd_rn(sb_.hw, sb_.hw)));
+                const int jrel = jb - sb_.base - (int)cb.jl;  // 0 or 1 when the ray meets this column
+                if (jrel != 0 && jrel != 1) continue;
                 float blo, bhi;
-                dcell_frac(sb_, b_increasing(rp), (float)(jb - sb_.base), blo, bhi);
+                cb.cell(jrel, blo, bhi);
                 if (!(bhi > blo)) continue;
                 // rows t whose height within row ia can meet [zc_lo, zc_hi]:
                 // zb(a) = u (Z0 + a Z1) + oz, a in [ia, ia+1], solved for u
@@ -349,15 +407,18 @@ __global__ void __launch_bounds__(256) bp3d_kernel(Geo3 g, const float *__restri
                 for (int t = t_lo; t <= t_hi; ++t) {
                     const ZRow z = zrow(rp, 2 * t - g.u0);
                     const DSpan sz_ = zspan(rp, z, ia);
-                    const int klo = sz_.base + (int)floorf(sz_.lo);
-                    const int khi = sz_.base + (int)floorf(sz_.hi);
-                    if (khi < kz0 || klo >= kz0 + KZ) continue;
-                    const bool zinc = z.inc;
+                    const SpanCells cz = span_cells(sz_, z.inc, rcp_approx(__fadd_rn(z.hwz, z.hwz)));
+                    const int k0 = sz_.base + (int)cz.jl;  // first slice the row meets
+                    const int nk = cz.two ? 2 : 1;
+                    if (k0 + nk - 1 < kz0 || k0 >= kz0 + KZ) continue;
                     const float val = __ldg(rv + (size_t)t * g.ns + c);
-                    const int q1 = min(khi, kz0 + KZ - 1) - kz0;
-                    for (int q = max(klo, kz0) - kz0; q <= q1; ++q) {
+#pragma unroll
+                    for (int bk = 0; bk < 2; ++bk) {
+                        if (bk == nk) break;
+                        const int q = k0 + bk - kz0;
+                        if ((unsigned)q >= (unsigned)KZ || k0 + bk >= g.nz) continue;
                         float zlo_, zhi_;
-                        dcell_frac(sz_, zinc, (float)(kz0 + q - sz_.base), zlo_, zhi_);
+                        cz.cell(bk, zlo_, zhi_);
                         acc[q * 256] = fmaf(pair_len(blo, bhi, zlo_, zhi_, z.L), val, acc[q * 256]);
                     }
                 }

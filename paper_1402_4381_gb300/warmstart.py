@@ -41,7 +41,7 @@ from . import roi, synth, workloads as W
 SCALE = 1.0 / synth.MU_WATER  # network units: water = 1
 HU = synth.HU
 THRESHOLDS = (20.0, 10.0, 5.0, 2.0, 1.0)
-FULL_REF_SCHEDULE = ((24, 100), (8, 100), (2, 200), (1, 2000))
+FULL_REF_SCHEDULE = ((24, 100), (8, 100), (2, 200))  # then the one-subset method to convergence
 ROUTE_SCHEDULE = ((24, 100), (8, 100), (2, 300))  # the subset-reduction route that reaches 1 HU
 
 
@@ -85,36 +85,61 @@ def _problem(oslalm, torch, geomh, wl, y, w, M=None, use_graph=True, storage=Non
                           delta=wl.delta, nbr=wl.nbr, M=M or wl.M, w_dtype=wd, d_dtype=dd, use_graph=use_graph)
 
 
-def run_batched(oslalm, torch, geomh, wls, scans, xs, schedule, chunk=64, storage=None, last_change=None):
+def run_batched(oslalm, torch, geomh, wls, scans, xs, schedule, chunk=64, storage=None):
     """Advance the images xs (in place) through `schedule` = ((M, iters), ...)
     with the batched persistent path, `chunk` scans per batch; a new M
-    restarts the method (init) from the current image.  last_change (a mask,
-    or None): also return, per scan, the RMS difference (HU) made by the
-    last quarter of the final stage."""
-    changes = []
+    restarts the method (init) from the current image."""
     for k in range(0, len(wls), chunk):
-        for si, (M, iters) in enumerate(schedule):
+        for M, iters in schedule:
             probs = [_problem(oslalm, torch, geomh, wl, y, w, M=M, use_graph=False, storage=storage)
                      for wl, (y, w) in zip(wls[k:k + chunk], scans[k:k + chunk])]
             for p, x in zip(probs, xs[k:k + chunk]):
                 p.init(x)
             b = oslalm.Batch(probs)
-            if last_change is not None and si == len(schedule) - 1:
-                q = iters // 4
-                b.iterate(xs[k:k + chunk], iters - q, use_graph=True)
-                before = [x.clone() for x in xs[k:k + chunk]]
-                b.iterate(xs[k:k + chunk], q, use_graph=True)
-                torch.cuda.synchronize()
-                m = torch.as_tensor(last_change.astype(np.uint8), device=before[0].device)
-                changes += [oslalm.rmsd(x, x_b, m) / HU for x, x_b in zip(xs[k:k + chunk], before)]
-                del before
-            else:
-                b.iterate(xs[k:k + chunk], iters, use_graph=True)
+            b.iterate(xs[k:k + chunk], iters, use_graph=True)
             torch.cuda.synchronize()
             b.close()
             for p in probs:
                 p.close()
-    return (xs, changes) if last_change is not None else xs
+    return xs
+
+
+def converge_batched(oslalm, torch, geomh, wls, scans, xs, mask_np, pre_schedule, block=500, tol_hu=0.01,
+                     max_iters=8000, chunk=64, storage=("f32", "f32")):
+    """Converged images x* (in place): `pre_schedule` (subset reduction),
+    then the one-subset method (Sec. III-A: it converges to the minimiser) in
+    blocks of `block` iterations, each scan keeping its method state, until
+    its image changes by less than tol_hu (RMS over the mask) in a block or
+    max_iters.  Returns per scan {"iterations", "last_change_hu",
+    "converged"}."""
+    run_batched(oslalm, torch, geomh, wls, scans, xs, pre_schedule, chunk, storage)
+    mask = torch.as_tensor(mask_np.astype(np.uint8), device=xs[0].device)
+    info = [None] * len(wls)
+    for k in range(0, len(wls), chunk):
+        idx = list(range(k, min(k + chunk, len(wls))))
+        probs = {i: _problem(oslalm, torch, geomh, wls[i], *scans[i], M=1, use_graph=False, storage=storage)
+                 for i in idx}
+        for i in idx:
+            probs[i].init(xs[i])
+        active, done = idx, 0
+        while active and done < max_iters:
+            before = {i: xs[i].clone() for i in active}
+            b = oslalm.Batch([probs[i] for i in active])
+            b.iterate([xs[i] for i in active], block, use_graph=True)
+            torch.cuda.synchronize()
+            b.close()
+            done += block
+            still = []
+            for i in active:
+                ch = oslalm.rmsd(xs[i], before[i], mask) / HU
+                info[i] = {"iterations": done, "last_change_hu": round(ch, 5), "converged": ch < tol_hu}
+                if ch >= tol_hu:
+                    still.append(i)
+            del before
+            active = still
+        for i in idx:
+            probs[i].close()
+    return info
 
 
 def train(torch, net, xs, ts, epochs, lr, batch, seed=0, log=None):
@@ -280,7 +305,8 @@ def paired_gain(fbp_rows, cnn_rows, thresholds=THRESHOLDS):
 
 
 def experiment(n_train=2000, n_test=100, target_iters=200, epochs=30, batch=8, lr=1e-3, nx=512, nviews=984,
-               ns=888, M=24, ref_schedule=FULL_REF_SCHEDULE, n_eval_iter=50, chunk=64, log=print):
+               ns=888, M=24, ref_schedule=FULL_REF_SCHEDULE, n_eval_iter=50, chunk=64, log=print,
+               ref_block=500, ref_tol_hu=0.01, ref_max_iters=8000, params_out=None):
     """The whole warm-start experiment; returns a JSON-ready dict."""
     base = base_workload(nx, nviews, ns, M)
     wls_tr = [scan_workload(s, base) for s in range(n_train)]
@@ -314,19 +340,25 @@ def experiment(n_train=2000, n_test=100, target_iters=200, epochs=30, batch=8, l
     def cnn_init(x0):
         return torch.clamp(inf.forward(x0.view(1, g.ny, g.nx), SCALE), min=0.0).view(x0.shape)
 
+    if params_out:
+        np.save(params_out, net.get_params())
     mask = roi.roi_mask(g)
     t0 = time.time()
-    xstars, ref_change = run_batched(oslalm, torch, geomh, wls_te, scans_te, [x.clone() for x in x0_te], ref_schedule,
-                                     chunk, storage=("f32", "f32"), last_change=mask)
+    xstars = [x.clone() for x in x0_te]
+    ref_info = converge_batched(oslalm, torch, geomh, wls_te, scans_te, xstars, mask, ref_schedule, ref_block,
+                                ref_tol_hu, ref_max_iters, chunk)
     t_ref = time.time() - t0
-    log(f"references: {t_ref:.1f} s; change over the last quarter of the final stage: max "
-        f"{max(ref_change):.4f} HU")
+    n_conv = sum(r["converged"] for r in ref_info)
+    log(f"references: {t_ref:.1f} s; {n_conv} of {len(ref_info)} converged (change < {ref_tol_hu} HU per "
+        f"{ref_block} iterations); iterations max {max(r['iterations'] for r in ref_info)}")
     fbp_rows = evaluate(oslalm, torch, geomh, wls_te, scans_te, x0_te, xstars, mask, None, n_eval_iter)
     cnn_rows = evaluate(oslalm, torch, geomh, wls_te, scans_te, x0_te, xstars, mask, cnn_init, n_eval_iter)
     t0 = time.time()
     fbp_route = evaluate_route(oslalm, torch, geomh, wls_te, scans_te, x0_te, xstars, mask, None)
     cnn_route = evaluate_route(oslalm, torch, geomh, wls_te, scans_te, x0_te, xstars, mask, cnn_init)
     log(f"route evaluation: {time.time() - t0:.1f} s")
+    ok = [i for i, r in enumerate(ref_info) if r["converged"]]  # scans with a verified x*
+    fbp_ok, cnn_ok = [fbp_route[i] for i in ok], [cnn_route[i] for i in ok]
     return {
         "geometry": {"image": [g.ny, g.nx], "views": g.nviews, "channels": g.ns, "M": M},
         "train": {"scans": n_train, "target_iterations": target_iters, "epochs": epochs, "batch": batch,
@@ -334,14 +366,18 @@ def experiment(n_train=2000, n_test=100, target_iters=200, epochs=30, batch=8, l
                   "loss_by_epoch": [round(v, 6) for v in hist]},
         "held_out": n_test, "reference_schedule": [list(s) for s in ref_schedule],
         "reference_storage": "f32",
-        "reference_last_quarter_change_hu": {"max": round(max(ref_change), 5),
-                                             "mean": round(float(np.mean(ref_change)), 5)},
+        "reference": {"then": f"one subset in blocks of {ref_block} iterations until the RMS change in a block "
+                              f"is below {ref_tol_hu} HU (at most {ref_max_iters})",
+                      "converged": n_conv, "of": len(ref_info),
+                      "iterations": [r["iterations"] for r in ref_info],
+                      "last_change_hu": [r["last_change_hu"] for r in ref_info]},
         "configured": {"M": M, "iterations": n_eval_iter, "storage": [base.w_dtype, base.d_dtype],
                        "fbp_init": summarize(fbp_rows), "cnn_init": summarize(cnn_rows),
                        "paired": paired_gain(fbp_rows, cnn_rows)},
         "route": {"schedule": [list(s) for s in ROUTE_SCHEDULE], "stop_hu": 1.0, "storage": "f32",
-                  "fbp_init": summarize_route(fbp_route), "cnn_init": summarize_route(cnn_route),
-                  "paired": paired_gain(fbp_route, cnn_route)},
+                  "scans": "the held-out scans whose x* converged",
+                  "fbp_init": summarize_route(fbp_ok), "cnn_init": summarize_route(cnn_ok),
+                  "paired": paired_gain(fbp_ok, cnn_ok)},
         "seconds": {"scan_generation_cpu": round(t_scan, 1), "targets_gpu": round(t_targets, 1),
                     "references_gpu": round(t_ref, 1)},
     }
@@ -361,9 +397,10 @@ def main(argv=None):
     ap.add_argument("--M", type=int, default=24)
     ap.add_argument("--eval-iters", type=int, default=50)
     ap.add_argument("--out", default=None)
+    ap.add_argument("--params-out", default=None, help="save the trained parameters (.npy)")
     a = ap.parse_args(argv)
     res = experiment(a.train, a.test, a.target_iters, a.epochs, a.batch, a.lr, a.nx, a.views, a.channels, a.M,
-                     n_eval_iter=a.eval_iters)
+                     n_eval_iter=a.eval_iters, params_out=a.params_out)
     s = json.dumps(res, indent=1)
     if a.out:
         with open(a.out, "w") as f:
