@@ -162,7 +162,7 @@ __global__ void __launch_bounds__(256) batch_forward_kernel(const SliceDesc *__r
 __global__ void __launch_bounds__(kBpThreads, 8) batch_backproject_kernel(const SliceDesc *__restrict__ S, int n,
                                                                        int step) {
     __shared__ int pre[kMaxSlices + 1];
-    __shared__ double red[32];
+    __shared__ float red[64];
     __shared__ BpTileAcc acc;
     const int total =
         work_prefix(S, n, step, [](const SliceDesc &d) { return slice_tiles<kBpTile, kBpTile>(d); }, pre);
@@ -189,7 +189,7 @@ __global__ void __launch_bounds__(kBpThreads, 8) batch_backproject_kernel(const 
             d.ua.g[p] = a * v + b * g_old;
             xi_local = (double)(g_old - v) * (double)(v - z_old);
         }
-        const double bs = block_sum2d(xi_local, red);  // ends with a barrier: acc is free again
+        const double bs = block_sum_df(xi_local, red);  // ends with a barrier: acc is free again
         if (tid == 0) d.ua.partials[t] = bs;
     }
 }
@@ -389,6 +389,8 @@ int oslalm_batch_create(oslalm_problem *const *probs, int n, oslalm_batch **out)
         a.rho_mode = p->p.rho_mode;
         a.rho_min = p->p.rho_min;
         a.rho_fixed = p->p.rho_fixed;
+        a.rho_tab = p->d_rho_tab;
+        a.rho_tab_n = p->rho_tab_n;
     }
     *out = b;
     return OSLALM_OK;

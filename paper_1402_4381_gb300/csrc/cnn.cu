@@ -297,23 +297,43 @@ int conv(const oslalm_cnn *c, const __nv_bfloat16 *in, int ld_in, int coff_in, i
     return OSLALM_OK;
 }
 
-int wgrad(const __nv_bfloat16 *dz, int cout, const __nv_bfloat16 *x, int ld_x, int coff_x, int cin, float *dw, int n,
-          int h, int wd, cudaStream_t st) {
+int wgrad(const oslalm_cnn *c, const __nv_bfloat16 *dz, int cout, const __nv_bfloat16 *x, int ld_x, int coff_x,
+          int cin, float *dw, int n, int h, int wd, cudaStream_t st) {
     WgradArgs a;
     a.dz = dz; a.ld_dz = cout; a.coff_dz = 0; a.cout = cout;
     a.x = x; a.ld_x = ld_x; a.coff_x = coff_x; a.cin = cin;
     a.dw = dw; a.n = n; a.h = h; a.wd = wd;
     const long P = (long)n * h * wd;
-    // about 4 blocks per SM of work in total
-    const long tiles = (long)((cout + 63) / 64) * 9 * (cin / 32);
+    // input channels per block: the largest power of two <= 256 dividing cin
+    int bn = 256;
+    while (cin % bn) bn >>= 1;
+    if (bn < 32 || cout % 8) return fail(OSLALM_ERR_ARG, "weight gradient needs channel counts that are multiples of 32");
+    // pixel ranges: about 4 blocks per SM of work in total
+    const long tiles = (long)((cout + 127) / 128) * 9 * (cin / bn);
     long splits = (152 * 4 + tiles - 1) / tiles;
     if (splits < 1) splits = 1;
     long per = (P + splits - 1) / splits;
     per = ((per + 31) / 32) * 32;
     a.pix_per_block = (int)per;
-    dim3 grid((cout + 63) / 64, 9 * (cin / 32), (unsigned)((P + per - 1) / per));
-    wgrad3x3_kernel<<<grid, 128, 0, st>>>(a);
-    OSL_LAUNCH_CHECK("wgrad3x3_kernel");
+    dim3 grid((cout + 127) / 128, 9 * (cin / bn), (unsigned)((P + per - 1) / per));
+#define OSL_WG(BN)                                                                                           \
+    do {                                                                                                     \
+        static bool opted = false;                                                                           \
+        if (!opted) {                                                                                        \
+            OSL_CUDA_TRY(cudaFuncSetAttribute(wgrad3x3_tc_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                              wgrad_tc_smem_bytes(BN)));                                     \
+            opted = true;                                                                                    \
+        }                                                                                                    \
+        wgrad3x3_tc_kernel<BN><<<grid, 128, wgrad_tc_smem_bytes(BN), st>>>(a, c->err);                      \
+    } while (0)
+    switch (bn) {
+        case 32: OSL_WG(32); break;
+        case 64: OSL_WG(64); break;
+        case 128: OSL_WG(128); break;
+        default: OSL_WG(256); break;
+    }
+#undef OSL_WG
+    OSL_LAUNCH_CHECK("wgrad3x3_tc_kernel");
     return OSLALM_OK;
 }
 
@@ -328,7 +348,7 @@ int layer_bwd(oslalm_cnn *c, int L, int lvl, const __nv_bfloat16 *x, int ld_x, i
     const long P = c->P[lvl];
     relu_bwd_kernel<<<nb(P * s.cout, 256), 256, 0, st>>>(y, ld_y, coff_y, gy, ld_gy, coff_gy, s.cout, P, c->dz);
     OSL_LAUNCH_CHECK("relu_bwd_kernel");
-    if (int rc = wgrad(c->dz, s.cout, x, ld_x, coff_x, s.cin, c->grad + c->off_w[L], c->batch, h, w, st)) return rc;
+    if (int rc = wgrad(c, c->dz, s.cout, x, ld_x, coff_x, s.cin, c->grad + c->off_w[L], c->batch, h, w, st)) return rc;
     bias_grad_kernel<<<std::min<long>(nb(P, 8), 2048), 256, 0, st>>>(c->dz, s.cout, P, c->grad + c->off_b[L]);
     OSL_LAUNCH_CHECK("bias_grad_kernel");
     if (gx)

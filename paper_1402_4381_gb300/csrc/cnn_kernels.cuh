@@ -10,8 +10,10 @@
 //   channels, double-buffered cp.async staging into the core-matrix layout,
 //   MMAs issued by one thread and tracked by mbarriers.  With transposed,
 //   tap-flipped weights the same kernel computes the data gradient.
-// wgrad3x3_kernel: dW[co][tap][ci] = sum_p dz[p][co] x[p + shift(tap)][ci],
-//   split over pixel ranges, partial tiles added with FP32 atomics.
+// wgrad3x3_tc_kernel: dW[co][tap][ci] = sum_p dz[p][co] x[p + shift(tap)][ci]
+//   on the tcgen05 tensor cores with both operands MN-major (pixel-major
+//   activations staged as they are), split over pixel ranges, partial tiles
+//   added with FP32 atomics.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -381,6 +383,136 @@ __global__ void __launch_bounds__(128) wgrad3x3_kernel(WgradArgs a) {
             atomicAdd(d, acc[nj][hrow * 2 + 0]);
             atomicAdd(d + 1, acc[nj][hrow * 2 + 1]);
         }
+}
+
+// Weight gradient on the tcgen05 tensor cores: for one tap and a slice of
+// 128 output channels (M, padded with zero rows) x BN input channels (N), a
+// block adds up dW[co][tap][ci] = sum_p dz[p][co] x[p + shift][ci] over a pixel
+// range (K) into a tensor-memory accumulator, then adds it to dw with FP32
+// atomics.  Both operands are stored pixel-major (channels contiguous), which
+// is the MN-major canonical layout without swizzle: a core matrix is 8 pixels
+// (K) x 16 bytes (8 channels, MN) = 128 contiguous bytes, so every 16-byte
+// chunk (8 channels of one pixel) is staged by cp.async straight into place:
+// K groups of 8 pixels 128 bytes apart (leading byte offset), MN groups of 8
+// channels 512 bytes apart (stride byte offset), 32 pixels per stage.  The
+// instruction descriptor marks A and B as MN-major.  Waits are bounded as in
+// conv3x3_kernel.
+__host__ __device__ constexpr int wgrad_tc_smem_bytes(int bn) { return 2 * (128 + bn) * 32 * 2 + 32; }
+
+template <int BN>
+__global__ void __launch_bounds__(128) wgrad3x3_tc_kernel(WgradArgs a, int *err) {
+    extern __shared__ __align__(1024) unsigned char sm[];
+    constexpr int BM = 128, BK = 32;
+    constexpr int A_BYTES = BM * BK * 2, B_BYTES = BN * BK * 2;
+    unsigned char *sA = sm, *sB = sm + 2 * A_BYTES;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sm + 2 * (A_BYTES + B_BYTES));
+    uint32_t *s_taddr = reinterpret_cast<uint32_t *>(bar + 2);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const long P = (long)a.n * a.h * a.wd;
+    const int co0 = blockIdx.x * BM;
+    const int tap = blockIdx.y / (a.cin / BN);
+    const int ci0 = (blockIdx.y % (a.cin / BN)) * BN;
+    const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+    const long pbeg = (long)blockIdx.z * a.pix_per_block;
+    const long pend = pbeg + a.pix_per_block < P ? pbeg + a.pix_per_block : P;
+    const int nk = (int)((pend - pbeg + BK - 1) / BK);
+    if (warp == 0) tc::tmem_alloc(s_taddr, BN);
+    if (tid < 2) tc::mbar_init(&bar[tid], 1);
+    tc::fence_barrier_init();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t taddr = *s_taddr;
+    auto load_stage = [&](int ks, int buf) {
+        const long pb = pbeg + (long)ks * BK;
+        unsigned char *A = sA + buf * A_BYTES;
+        unsigned char *B = sB + buf * B_BYTES;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {  // A: 32 pixels x 16 groups of 8 output channels
+            const int idx = tid + q * 128;
+            const int px = idx >> 4, cg = idx & 15;
+            const long p = pb + px;
+            const bool ok = p < pend && co0 + cg * 8 < a.cout;
+            const __nv_bfloat16 *g = a.dz + (ok ? p : 0) * a.ld_dz + a.coff_dz + (ok ? co0 + cg * 8 : 0);
+            cp_async16(A + cg * 512 + (px >> 3) * 128 + (px & 7) * 16, g, ok);
+        }
+#pragma unroll
+        for (int q = 0; q < BN / 32; ++q) {  // B: 32 pixels x BN/8 groups of 8 input channels
+            const int idx = tid + q * 128;
+            const int px = idx / (BN / 8), cg = idx % (BN / 8);
+            const long p = pb + px;
+            bool ok = p < pend;
+            long src = 0;
+            if (ok) {
+                const int xq = (int)(p % a.wd);
+                const int yq = (int)((p / a.wd) % a.h);
+                ok = yq + dy >= 0 && yq + dy < a.h && xq + dx >= 0 && xq + dx < a.wd;
+                src = p + (long)dy * a.wd + dx;
+            }
+            const __nv_bfloat16 *g = a.x + (ok ? src : 0) * a.ld_x + a.coff_x + ci0 + cg * 8;
+            cp_async16(B + cg * 512 + (px >> 3) * 128 + (px & 7) * 16, g, ok);
+        }
+        cp_async_commit();
+    };
+    constexpr uint32_t idesc = tc::idesc_bf16(BM, BN) | (1u << 15) | (1u << 16);  // A and B MN-major
+    bool ok = true;
+    int last = -1;  // last K step whose MMAs were committed
+    if (nk > 0) load_stage(0, 0);
+    for (int ks = 0; ks < nk; ++ks) {
+        const int buf = ks & 1;
+        if (ks + 1 < nk) {
+            if (ks >= 1) ok = tc::mbar_wait(&bar[buf ^ 1], ((ks - 1) >> 1) & 1);
+            if (!__syncthreads_and(ok)) {
+                ok = false;
+                break;
+            }
+            load_stage(ks + 1, buf ^ 1);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        tc::fence_proxy_async();
+        __syncthreads();
+        if (tid == 0) {
+            tc::fence_after_sync();
+            const unsigned char *A = sA + buf * A_BYTES, *B = sB + buf * B_BYTES;
+#pragma unroll
+            for (int kh = 0; kh < BK / 16; ++kh)  // 16 pixels (two K groups) per MMA
+                tc::mma_bf16(taddr, tc::smem_desc(A + kh * 256, 128, 512), tc::smem_desc(B + kh * 256, 128, 512),
+                             idesc, (ks > 0 || kh > 0) ? 1u : 0u);
+            tc::mma_commit(&bar[buf]);
+        }
+        last = ks;
+    }
+    if (ok && nk > 0) ok = tc::mbar_wait(&bar[(nk - 1) & 1], ((nk - 1) >> 1) & 1);
+    if (!__syncthreads_and(ok)) {
+        // a wait ran out: flag, let the copies land, one more bounded wait for
+        // the committed MMAs, release the tensor memory, add nothing
+        if (tid == 0) atomicOr(err, 1);
+        cp_async_wait<0>();
+        if (last >= 0) tc::mbar_wait(&bar[last & 1], (last >> 1) & 1);
+        tc::fence_before_sync();
+        __syncthreads();
+        if (warp == 0) tc::tmem_dealloc(taddr, BN);
+        return;
+    }
+    tc::fence_after_sync();
+    if (nk > 0) {
+        const int co = co0 + warp * 32 + lane;  // this thread's accumulator row (tensor-memory lane)
+#pragma unroll 1
+        for (int c = 0; c < BN; c += 8) {
+            float v[8];
+            tc::tmem_ld8(taddr + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, v);
+            if (co < a.cout) {
+                float *d = a.dw + ((long)co * 9 + tap) * a.cin + ci0 + c;
+#pragma unroll
+                for (int i = 0; i < 8; ++i) atomicAdd(d + i, v[i]);
+            }
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(taddr, BN);
 }
 
 }  // namespace cnn

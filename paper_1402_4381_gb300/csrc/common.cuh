@@ -225,6 +225,15 @@ __device__ __forceinline__ void refresh_rho_factors(DevState *st) {
     st->gb = (float)(1.0 / (rho + 1.0));
 }
 
+// The continuation's rho_l and its g-update weights for l = 0 .. n-1, formed
+// on the host in FP64 with the same operations as rho_of_l and
+// refresh_rho_factors (so the same bits): the last block of a
+// subset-iteration looks them up instead of dividing in FP64.
+struct RhoEnt {
+    double rho;
+    float ga, gb;  // (float)(rho/(rho+1)), (float)(1/(rho+1))
+};
+
 struct UpdateArgs {  // epilogue arguments of the fused back-projection
     float *zeta;
     float *g;
@@ -251,6 +260,8 @@ struct UpdateArgs {  // epilogue arguments of the fused back-projection
     const void *D;
     int d_dtype;
     const float *dscale;
+    const RhoEnt *rho_tab;  // rho_l for l < rho_tab_n (continuation and replay modes), or null
+    int rho_tab_n;
 };
 
 int launch_fp2d(const Geo2 &g, const float *x, float *out, const int *views, int nv,

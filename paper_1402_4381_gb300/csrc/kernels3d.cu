@@ -342,7 +342,7 @@ __global__ void __launch_bounds__(128) cost3d_kernel(Geo3 g, const float *__rest
 }
 
 // ---------------------------------------------------------------- back-projection
-constexpr int KZ = 8;  // voxels per thread along z
+constexpr int KZ = 32;  // voxels per thread along z
 
 template <int MODE>
 __global__ void __launch_bounds__(256) bp3d_kernel(Geo3 g, const float *__restrict__ r, float *__restrict__ out,

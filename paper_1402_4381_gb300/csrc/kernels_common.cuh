@@ -49,6 +49,48 @@ __device__ __forceinline__ double block_sum2d(double v, double *red) {
     return t;
 }
 
+// Sum of FP64 values over a block in FP32 double-float arithmetic (each value
+// split into hi + lo floats, pairs added with Knuth's error-free two-sum and
+// renormalised), for the per-subset-iteration reductions: FP64 throughput is
+// scarce on this GPU, and the pair keeps about 2^-44 relative accuracy.  Fixed
+// order: deterministic.  Result valid in thread (0, 0) of the block; red holds
+// 2 x 32 floats of caller scratch.
+__device__ __forceinline__ void df_add(float &hi, float &lo, float h2, float l2) {
+    const float s = __fadd_rn(hi, h2);
+    const float bb = __fsub_rn(s, hi);
+    const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(h2, bb));
+    const float t = __fadd_rn(__fadd_rn(lo, l2), e);
+    hi = __fadd_rn(s, t);
+    lo = __fsub_rn(t, __fsub_rn(hi, s));
+}
+
+__device__ __forceinline__ double block_sum_df(double v, float *red) {
+    const int tid = (threadIdx.z * blockDim.y + threadIdx.y) * blockDim.x + threadIdx.x;
+    const int nt = blockDim.x * blockDim.y * blockDim.z;
+    float hi = (float)v;
+    float lo = (float)(v - (double)hi);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        df_add(hi, lo, __shfl_xor_sync(0xffffffffu, hi, o), __shfl_xor_sync(0xffffffffu, lo, o));
+    if ((tid & 31) == 0) {
+        red[tid >> 5] = hi;
+        red[32 + (tid >> 5)] = lo;
+    }
+    __syncthreads();
+    double t = 0.0;
+    if (tid < 32) {
+        const bool in = tid < (nt + 31) / 32;
+        hi = in ? red[tid] : 0.f;
+        lo = in ? red[32 + tid] : 0.f;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+            df_add(hi, lo, __shfl_xor_sync(0xffffffffu, hi, o), __shfl_xor_sync(0xffffffffu, lo, o));
+        t = (double)hi + (double)lo;
+    }
+    __syncthreads();
+    return t;
+}
+
 // hyperbola potential psi(t) = delta^2 (sqrt(1 + (t/delta)^2) - 1), written
 // without the cancellation of the difference
 __device__ __forceinline__ double hyperbola(double t, double delta) {
@@ -115,6 +157,7 @@ __device__ __forceinline__ void add_iter_terms(const UpdateArgs &ua, size_t p, f
 // or 1 when s'y <= 0 or s'Ds = 0.  One thread writes the state.
 __device__ __forceinline__ void finish_subset_iteration(const UpdateArgs &ua, int nblocks) {
     __shared__ double red_last[32];
+    __shared__ float red_df[64];
     double v = 0.0, vy = 0.0, vd = 0.0;
     const int nt = blockDim.x * blockDim.y * blockDim.z;
     const int tid = (threadIdx.z * blockDim.y + threadIdx.y) * blockDim.x + threadIdx.x;
@@ -125,7 +168,7 @@ __device__ __forceinline__ void finish_subset_iteration(const UpdateArgs &ua, in
             vd += __ldcg(ua.partials + 2 * nblocks + i);
         }
     }
-    v = block_sum2d(v, red_last);
+    v = block_sum_df(v, red_df);
     if (ua.bb) {
         vy = block_sum2d(vy, red_last);
         vd = block_sum2d(vd, red_last);
@@ -143,9 +186,10 @@ __device__ __forceinline__ void finish_subset_iteration(const UpdateArgs &ua, in
         } else if (ua.rho_mode == OSLALM_RHO_REPLAY) {
             restart = (ua.replay && j < ua.replay_n) ? (ua.replay[j] != 0) : 0;
         }
+        const bool tab = ua.rho_mode != OSLALM_RHO_FIXED && ua.rho_tab && l + 1 < ua.rho_tab_n;
         if (ua.rho_mode != OSLALM_RHO_FIXED) {
             l = restart ? 0 : l + 1;
-            rho = rho_of_l(l, ua.rho_min);
+            rho = tab ? ua.rho_tab[l].rho : rho_of_l(l, ua.rho_min);
         }
         if (ua.bb) {  // refit H = alpha D at the end of every iteration
             st->bb_num += vy;
@@ -161,7 +205,14 @@ __device__ __forceinline__ void finish_subset_iteration(const UpdateArgs &ua, in
         st->xi = xi;
         st->l = l;
         st->rho = rho;
-        refresh_rho_factors(st);
+        if (tab) {  // the same values refresh_rho_factors forms, from the host's table
+            st->rho_f = (float)rho;
+            st->rho_d_f = st->alpha == 1.0 ? st->rho_f : (float)(rho * st->alpha);
+            st->ga = ua.rho_tab[l].ga;
+            st->gb = ua.rho_tab[l].gb;
+        } else if (ua.rho_mode != OSLALM_RHO_FIXED || ua.bb) {
+            refresh_rho_factors(st);
+        }
         if (ua.stats && ua.stats_cap > 0) {
             oslalm_stats rec;
             rec.xi = xi;
@@ -183,8 +234,9 @@ __device__ __forceinline__ void finish_subset_iteration(const UpdateArgs &ua, in
 // to arrive finishes the subset-iteration.  Called by every thread.
 __device__ __forceinline__ void subset_iteration_epilogue(const UpdateArgs &ua, const IterSums &loc) {
     __shared__ double red[32];
+    __shared__ float red_df[64];
     __shared__ int is_last;
-    const double bs = block_sum2d(loc.xi, red);
+    const double bs = block_sum_df(loc.xi, red_df);
     double by = 0.0, bd = 0.0;
     if (ua.bb) {
         by = block_sum2d(loc.sy, red);

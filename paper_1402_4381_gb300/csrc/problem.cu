@@ -194,6 +194,8 @@ UpdateArgs update_args(oslalm_problem *p, int subset) {
     a.D = p->d_D;
     a.d_dtype = p->p.d_dtype;
     a.dscale = p->d_dscale;
+    a.rho_tab = p->d_rho_tab;
+    a.rho_tab_n = p->rho_tab_n;
     return a;
 }
 
@@ -362,7 +364,7 @@ void free_problem(oslalm_problem *p) {
     cudaFree(p->d_r); cudaFree(p->d_tmp); cudaFree(p->d_state); cudaFree(p->d_partials); cudaFree(p->d_stats);
     cudaFree(p->d_replay);
     cudaFree(p->d_fu[0]); cudaFree(p->d_fu[1]); cudaFree(p->d_fv[0]); cudaFree(p->d_fv[1]);
-    cudaFree(p->d_bbx); cudaFree(p->d_bbz); cudaFree(p->d_bbhave);
+    cudaFree(p->d_bbx); cudaFree(p->d_bbz); cudaFree(p->d_bbhave); cudaFree(p->d_rho_tab);
     delete p;
 }
 
@@ -480,6 +482,32 @@ int oslalm_problem_create(const oslalm_geom *g, const float *y, const float *w, 
     if (e != cudaSuccess) {
         free_problem(p);
         return fail(OSLALM_ERR_ALLOC, "device allocation failed: %s", cudaGetErrorString(e));
+    }
+    if (pp.rho_mode != OSLALM_RHO_FIXED) {
+        // rho_l of the continuation (Eq. rho_l_formula_qp) up to the first l at
+        // which it reaches rho_min (at most 65536 entries), with the weights of
+        // the g-update, in the operations of the device's rho_of_l
+        std::vector<RhoEnt> tab;
+        for (int l = 0; l < 65536; ++l) {
+            double rho = 1.0;
+            if (l > 0) {
+                const double pi = 3.14159265358979323846;
+                const double a = pi / (double)(l + 1), b = pi / (double)(2 * l + 2);
+                const double v = a * sqrt(1.0 - b * b);
+                rho = v > pp.rho_min ? v : pp.rho_min;
+            }
+            tab.push_back(RhoEnt{rho, (float)(rho / (rho + 1.0)), (float)(1.0 / (rho + 1.0))});
+            if (l > 0 && rho == pp.rho_min) break;
+        }
+        if (e == cudaSuccess) e = cudaMalloc((void **)&p->d_rho_tab, sizeof(RhoEnt) * tab.size());
+        if (e == cudaSuccess) e = cudaMemcpy(p->d_rho_tab, tab.data(), sizeof(RhoEnt) * tab.size(), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            free_problem(p);
+            return fail(OSLALM_ERR_ALLOC, "continuation table: %s", cudaGetErrorString(e));
+        }
+        // past the last entry rho stays at rho_min; the device reads the table
+        // only for l + 1 < rho_tab_n and otherwise forms rho_l itself
+        p->rho_tab_n = (int)tab.size();
     }
     if ((e = cudaMemcpy(p->d_views, perm.data(), sizeof(int) * d.nviews, cudaMemcpyHostToDevice)) != cudaSuccess) {
         free_problem(p);

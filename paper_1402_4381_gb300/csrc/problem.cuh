@@ -27,6 +27,8 @@ struct oslalm_problem {
     float *d_r = nullptr;    // residual of one subset
     float *d_tmp = nullptr;  // full-sinogram scratch (set_data staging)
     oslalm::DevState *d_state = nullptr;
+    oslalm::RhoEnt *d_rho_tab = nullptr;  // continuation: rho_l and g-update weights for l < rho_tab_n
+    int rho_tab_n = 0;
     double *d_partials = nullptr;
     int n_partials = 0;
     oslalm_stats *d_stats = nullptr;
