@@ -42,7 +42,7 @@ SCALE = 1.0 / synth.MU_WATER  # network units: water = 1
 HU = synth.HU
 THRESHOLDS = (20.0, 10.0, 5.0, 2.0, 1.0)
 FULL_REF_SCHEDULE = ((24, 100), (8, 100), (2, 200))  # then the one-subset method to convergence
-ROUTE_SCHEDULE = ((24, 100), (8, 100), (2, 300))  # the subset-reduction route that reaches 1 HU
+ROUTE_SCHEDULE = ((24, 100), (8, 100), (2, 300), (1, 2000))  # the subset-reduction route that reaches 1 HU
 
 
 def base_workload(nx=512, nviews=984, ns=888, M=24) -> W.Workload:
@@ -306,9 +306,13 @@ def paired_gain(fbp_rows, cnn_rows, thresholds=THRESHOLDS):
 
 def experiment(n_train=2000, n_test=100, target_iters=200, epochs=30, batch=8, lr=1e-3, nx=512, nviews=984,
                ns=888, M=24, ref_schedule=FULL_REF_SCHEDULE, n_eval_iter=50, chunk=64, log=print,
-               ref_block=500, ref_tol_hu=0.01, ref_max_iters=8000, params_out=None):
-    """The whole warm-start experiment; returns a JSON-ready dict."""
+               ref_block=500, ref_tol_hu=0.01, ref_max_iters=8000, params_out=None, params_in=None):
+    """The whole warm-start experiment; returns a JSON-ready dict.  With
+    `params_in` (parameters saved by an earlier run) the training part is
+    skipped and the saved network is evaluated."""
     base = base_workload(nx, nviews, ns, M)
+    if params_in:
+        n_train = 0
     wls_tr = [scan_workload(s, base) for s in range(n_train)]
     wls_te = [scan_workload(1_000_000 + s, base) for s in range(n_test)]
     t0 = time.time()
@@ -325,23 +329,27 @@ def experiment(n_train=2000, n_test=100, target_iters=200, epochs=30, batch=8, l
     x0_tr = [geomh.fbp(torch.as_tensor(y, device=dev), clip=True) for y, _ in scans_tr]
     x0_te = [geomh.fbp(torch.as_tensor(y, device=dev), clip=True) for y, _ in scans_te]
     torch.cuda.synchronize()
-    t0 = time.time()
-    targets = run_batched(oslalm, torch, geomh, wls_tr, scans_tr, [x.clone() for x in x0_tr],
-                          ((M, target_iters),), chunk)
-    t_targets = time.time() - t0
-    log(f"targets: {t_targets:.1f} s")
-    net = oslalm.WarmStartNet(batch, g.ny, g.nx, seed=0)
-    hist, steps, t_train = train(torch, net, x0_tr, targets, epochs, lr, batch, log=log)
-    flops = 3.0 * oslalm.WarmStartNet.flops_per_image(g.ny, g.nx) * batch * steps
-    del targets
     inf = oslalm.WarmStartNet(1, g.ny, g.nx, seed=0)
-    inf.set_params(net.get_params())
+    if params_in:
+        inf.set_params(np.load(params_in))
+        hist, steps, t_train, t_targets, flops = [], 0, 0.0, 0.0, 0.0
+    else:
+        t0 = time.time()
+        targets = run_batched(oslalm, torch, geomh, wls_tr, scans_tr, [x.clone() for x in x0_tr],
+                              ((M, target_iters),), chunk)
+        t_targets = time.time() - t0
+        log(f"targets: {t_targets:.1f} s")
+        net = oslalm.WarmStartNet(batch, g.ny, g.nx, seed=0)
+        hist, steps, t_train = train(torch, net, x0_tr, targets, epochs, lr, batch, log=log)
+        flops = 3.0 * oslalm.WarmStartNet.flops_per_image(g.ny, g.nx) * batch * steps
+        del targets
+        inf.set_params(net.get_params())
+        if params_out:
+            np.save(params_out, net.get_params())
 
     def cnn_init(x0):
         return torch.clamp(inf.forward(x0.view(1, g.ny, g.nx), SCALE), min=0.0).view(x0.shape)
 
-    if params_out:
-        np.save(params_out, net.get_params())
     mask = roi.roi_mask(g)
     t0 = time.time()
     xstars = [x.clone() for x in x0_te]
@@ -362,7 +370,9 @@ def experiment(n_train=2000, n_test=100, target_iters=200, epochs=30, batch=8, l
     return {
         "geometry": {"image": [g.ny, g.nx], "views": g.nviews, "channels": g.ns, "M": M},
         "train": {"scans": n_train, "target_iterations": target_iters, "epochs": epochs, "batch": batch,
-                  "steps": steps, "seconds": round(t_train, 2), "tflops_bf16": round(flops / t_train / 1e12, 2),
+                  "steps": steps, "seconds": round(t_train, 2),
+                  "tflops_bf16": round(flops / t_train / 1e12, 2) if t_train > 0 else None,
+                  "params_in": params_in,
                   "loss_by_epoch": [round(v, 6) for v in hist]},
         "held_out": n_test, "reference_schedule": [list(s) for s in ref_schedule],
         "reference_storage": "f32",
@@ -398,9 +408,10 @@ def main(argv=None):
     ap.add_argument("--eval-iters", type=int, default=50)
     ap.add_argument("--out", default=None)
     ap.add_argument("--params-out", default=None, help="save the trained parameters (.npy)")
+    ap.add_argument("--params-in", default=None, help="evaluate saved parameters (.npy) instead of training")
     a = ap.parse_args(argv)
     res = experiment(a.train, a.test, a.target_iters, a.epochs, a.batch, a.lr, a.nx, a.views, a.channels, a.M,
-                     n_eval_iter=a.eval_iters, params_out=a.params_out)
+                     n_eval_iter=a.eval_iters, params_out=a.params_out, params_in=a.params_in)
     s = json.dumps(res, indent=1)
     if a.out:
         with open(a.out, "w") as f:
