@@ -308,29 +308,54 @@ int wgrad(const oslalm_cnn *c, const __nv_bfloat16 *dz, int cout, const __nv_bfl
     int bn = 256;
     while (cin % bn) bn >>= 1;
     if (bn < 32 || cout % 8) return fail(OSLALM_ERR_ARG, "weight gradient needs channel counts that are multiples of 32");
-    // pixel ranges: about 4 blocks per SM of work in total
+    // dz channel groups staged per block: 4, 8 or 16 (output channel counts
+    // of 32, 64 or a multiple of 128 ... any multiple of 8 from 128 on)
+    const int ga = wgrad_groups(cout);
+    if (ga != 4 && ga != 8 && ga != 16)
+        return fail(OSLALM_ERR_ARG, "weight gradient needs 32, 64 or at least 128 output channels");
+    const int smem = wgrad_tc_smem_bytes(bn, ga);
     const long tiles = (long)((cout + 127) / 128) * 9 * (cin / bn);
-    long splits = (152 * 4 + tiles - 1) / tiles;
+    // blocks per SM: shared memory (1 KB reserved per block), tensor-memory
+    // columns (512 per SM), 16 blocks of 128 threads
+    int dev = 0, sms = 0, smem_sm = 0;
+    OSL_CUDA_TRY(cudaGetDevice(&dev));
+    OSL_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    OSL_CUDA_TRY(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+    int occ = smem_sm / (smem + 1024);
+    occ = std::min(occ, std::min(512 / bn, 16));
+    if (occ < 1) occ = 1;
+    // one wave of blocks, the pixels split evenly (multiples of the 64-pixel
+    // stage) over the splits
+    long splits = ((long)sms * occ) / tiles;
     if (splits < 1) splits = 1;
     long per = (P + splits - 1) / splits;
-    per = ((per + 31) / 32) * 32;
+    per = ((per + kWgBK - 1) / kWgBK) * kWgBK;
     a.pix_per_block = (int)per;
-    dim3 grid((cout + 127) / 128, 9 * (cin / bn), (unsigned)((P + per - 1) / per));
-#define OSL_WG(BN)                                                                                           \
+    const dim3 grid((cout + 127) / 128, 9 * (cin / bn), (unsigned)((P + per - 1) / per));
+#define OSL_WG(BN, GA)                                                                                       \
     do {                                                                                                     \
-        static bool opted = false;                                                                           \
+        static bool opted = false; /* dynamic shared memory above 48 KB, once */                            \
         if (!opted) {                                                                                        \
-            OSL_CUDA_TRY(cudaFuncSetAttribute(wgrad3x3_tc_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                              wgrad_tc_smem_bytes(BN)));                                     \
+            OSL_CUDA_TRY(cudaFuncSetAttribute(wgrad3x3_tc_kernel<BN, GA>,                                    \
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize,                   \
+                                              wgrad_tc_smem_bytes(BN, GA)));                                 \
             opted = true;                                                                                    \
         }                                                                                                    \
-        wgrad3x3_tc_kernel<BN><<<grid, 128, wgrad_tc_smem_bytes(BN), st>>>(a, c->err);                      \
+        wgrad3x3_tc_kernel<BN, GA><<<grid, 128, wgrad_tc_smem_bytes(BN, GA), st>>>(a, c->err);              \
     } while (0)
-    switch (bn) {
-        case 32: OSL_WG(32); break;
-        case 64: OSL_WG(64); break;
-        case 128: OSL_WG(128); break;
-        default: OSL_WG(256); break;
+    switch (bn * 100 + ga) {
+        case 3204: OSL_WG(32, 4); break;
+        case 3208: OSL_WG(32, 8); break;
+        case 3216: OSL_WG(32, 16); break;
+        case 6404: OSL_WG(64, 4); break;
+        case 6408: OSL_WG(64, 8); break;
+        case 6416: OSL_WG(64, 16); break;
+        case 12804: OSL_WG(128, 4); break;
+        case 12808: OSL_WG(128, 8); break;
+        case 12816: OSL_WG(128, 16); break;
+        case 25604: OSL_WG(256, 4); break;
+        case 25608: OSL_WG(256, 8); break;
+        default: OSL_WG(256, 16); break;
     }
 #undef OSL_WG
     OSL_LAUNCH_CHECK("wgrad3x3_tc_kernel");

@@ -32,25 +32,6 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
 
-__device__ __forceinline__ void ldsm_x4(uint32_t &r0, uint32_t &r1, uint32_t &r2, uint32_t &r3, const void *p) {
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
-                 : "r"(smem_u32(p)));
-}
-__device__ __forceinline__ void ldsm_x4_t(uint32_t &r0, uint32_t &r1, uint32_t &r2, uint32_t &r3, const void *p) {
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
-                 : "r"(smem_u32(p)));
-}
-
-__device__ __forceinline__ void mma16816(float *c, const uint32_t *a, uint32_t b0, uint32_t b1) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};\n"
-        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
 struct ConvArgs {
     const __nv_bfloat16 *in;  // NHWC, channel slice [coff_in, coff_in + cin) of ld_in channels
     int ld_in, coff_in, cin;
@@ -81,10 +62,33 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity) {
         : "memory");
     return ok != 0;
 }
-// bounded: each try suspends for a bounded time, the loop ends in well under a second
+// the same, but a thread whose phase is not complete sleeps until it completes
+// or for at most `ns` nanoseconds, instead of coming back at once
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t *bar, unsigned parity, unsigned ns) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(ns)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// bounded wait: false after half a second of the global timer (or 2^24 tries,
+// should the timer not advance), so a block can never hang on a phase that
+// does not complete; waiting threads sleep rather than spin, leaving the
+// issue slots to the other blocks on the SM
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity) {
-    for (int i = 0; i < (1 << 22); ++i)
-        if (mbar_try_wait(bar, parity)) return true;
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    for (int i = 0; i < (1 << 24); ++i) {
+        if (mbar_try_wait_sleep(bar, parity, 2000)) return true;
+        if (global_ns() - t0 > 500000000ull) return false;
+    }
     return false;
 }
 __device__ __forceinline__ void fence_barrier_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
@@ -175,35 +179,37 @@ __global__ void __launch_bounds__(128) conv3x3_kernel(ConvArgs a, int *err) {
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t taddr = *s_taddr;
+    // this thread's 4 pixel rows (row = tid / 4 + 32 q, chunk tid % 4) are the
+    // same in every K step: their image coordinates are found once
+    const int ch = tid & 3;
+    int px[4], py[4];
+    const __nv_bfloat16 *pin[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const long p = p0 + (tid >> 2) + 32 * q;
+        const bool in = p < P;
+        px[q] = in ? (int)(p % a.wd) : -4;  // -4: outside the image for every tap
+        py[q] = in ? (int)((p / a.wd) % a.h) : 0;
+        pin[q] = a.in + (in ? p : 0) * a.ld_in + a.coff_in + ch * 8;
+    }
     auto load_stage = [&](int ks, int buf) {
         const int tap = ks / csteps, ci0 = (ks % csteps) * kBK;
         const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+        const long shift = ((long)dy * a.wd + dx) * a.ld_in + ci0;
         unsigned char *A = sA + buf * A_BYTES;
         unsigned char *B = sB + buf * B_BYTES;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {  // 128 rows x 4 chunks of 8 channels
-            const int idx = tid + q * 128;
-            const int row = idx >> 2, ch = idx & 3;
-            const long p = p0 + row;
-            bool ok = p < P;
-            long src = 0;
-            if (ok) {
-                const int x = (int)(p % a.wd);
-                const long t = p / a.wd;
-                const int y = (int)(t % a.h);
-                const int yy = y + dy, xx = x + dx;
-                ok = yy >= 0 && yy < a.h && xx >= 0 && xx < a.wd;
-                src = p + (long)dy * a.wd + dx;
-            }
-            const __nv_bfloat16 *g = a.in + (ok ? src : 0) * a.ld_in + a.coff_in + ci0 + ch * 8;
-            cp_async16(A + (row >> 3) * 512 + ch * 128 + (row & 7) * 16, g, ok);
+            const int row = (tid >> 2) + 32 * q;
+            const bool ok = (unsigned)(py[q] + dy) < (unsigned)a.h && (unsigned)(px[q] + dx) < (unsigned)a.wd;
+            cp_async16(A + (row >> 3) * 512 + ch * 128 + (row & 7) * 16, ok ? pin[q] + shift : a.in, ok);
         }
 #pragma unroll
         for (int q = 0; q < BN / 32; ++q) {  // BN rows x 4 chunks
             const int idx = tid + q * 128;
-            const int row = idx >> 2, ch = idx & 3;
-            const __nv_bfloat16 *g = a.w + ((long)(co0 + row) * 9 + tap) * a.cin + ci0 + ch * 8;
-            cp_async16(B + (row >> 3) * 512 + ch * 128 + (row & 7) * 16, g, true);
+            const int row = idx >> 2, cb = idx & 3;
+            const __nv_bfloat16 *g = a.w + ((long)(co0 + row) * 9 + tap) * a.cin + ci0 + cb * 8;
+            cp_async16(B + (row >> 3) * 512 + cb * 128 + (row & 7) * 16, g, true);
         }
         cp_async_commit();
     };
@@ -293,120 +299,58 @@ struct WgradArgs {
     int pix_per_block;
 };
 
-// block: 64 output channels x 32 input channels of one tap, over a pixel range
-__global__ void __launch_bounds__(128) wgrad3x3_kernel(WgradArgs a) {
-    constexpr int BM = 64, BN = 32, BK = 32;
-    __shared__ __align__(16) __nv_bfloat16 sA[2][BK * 72];  // [p][co], row stride 72 (64 + 8)
-    __shared__ __align__(16) __nv_bfloat16 sB[2][BK * 40];  // [p][ci], row stride 40
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const long P = (long)a.n * a.h * a.wd;
-    const int co0 = blockIdx.x * BM;
-    const int tap = blockIdx.y / (a.cin / BN);
-    const int ci0 = (blockIdx.y % (a.cin / BN)) * BN;
-    const int dy = tap / 3 - 1, dx = tap % 3 - 1;
-    const long pbeg = (long)blockIdx.z * a.pix_per_block;
-    const long pend = pbeg + a.pix_per_block < P ? pbeg + a.pix_per_block : P;
-    const int nk = (int)((pend - pbeg + BK - 1) / BK);
-    auto load_stage = [&](int ks, int buf) {
-        const long pb = pbeg + (long)ks * BK;
-        // A: 32 pixels x 64 channels of dz = 256 chunks -> 2 per thread
-#pragma unroll
-        for (int q = 0; q < 2; ++q) {
-            const int idx = tid + q * 128;
-            const int row = idx >> 3, ch = idx & 7;
-            const long p = pb + row;
-            const bool ok = p < pend && co0 + ch * 8 < a.cout;
-            const __nv_bfloat16 *g = a.dz + (ok ? p : 0) * a.ld_dz + a.coff_dz + (ok ? co0 + ch * 8 : 0);
-            cp_async16(&sA[buf][row * 72 + ch * 8], g, ok);
-        }
-        // B: 32 pixels x 32 channels of x at the tap shift = 128 chunks -> 1 per thread
-        {
-            const int row = tid >> 2, ch = tid & 3;
-            const long p = pb + row;
-            bool ok = p < pend;
-            long src = 0;
-            if (ok) {
-                const int xq = (int)(p % a.wd);
-                const int yq = (int)((p / a.wd) % a.h);
-                ok = yq + dy >= 0 && yq + dy < a.h && xq + dx >= 0 && xq + dx < a.wd;
-                src = p + (long)dy * a.wd + dx;
-            }
-            const __nv_bfloat16 *g = a.x + (ok ? src : 0) * a.ld_x + a.coff_x + ci0 + ch * 8;
-            cp_async16(&sB[buf][row * 40 + ch * 8], g, ok);
-        }
-        cp_async_commit();
-    };
-    float acc[4][4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-#pragma unroll
-        for (int k = 0; k < 4; ++k) acc[j][k] = 0.f;
-    if (nk > 0) load_stage(0, 0);
-    for (int ks = 0; ks < nk; ++ks) {
-        const int buf = ks & 1;
-        if (ks + 1 < nk) {
-            load_stage(ks + 1, buf ^ 1);
-            cp_async_wait<1>();
-        } else {
-            cp_async_wait<0>();
-        }
-        __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < BK; kk += 16) {
-            // A fragment (16 co x 16 p) from sA[p][co] by transposed loads
-            uint32_t af[4];
-            {
-                const int prow = kk + (lane & 7) + ((lane >> 4) << 3);
-                const int col = warp * 16 + ((lane >> 3) & 1) * 8;
-                ldsm_x4_t(af[0], af[1], af[2], af[3], &sA[buf][prow * 72 + col]);
-            }
-            uint32_t bf[4][2];
-#pragma unroll
-            for (int nj = 0; nj < 4; nj += 2) {
-                const int prow = kk + (lane & 7) + (((lane >> 3) & 1) << 3);
-                const int col = nj * 8 + ((lane >> 4) << 3);
-                ldsm_x4_t(bf[nj][0], bf[nj][1], bf[nj + 1][0], bf[nj + 1][1], &sB[buf][prow * 40 + col]);
-            }
-#pragma unroll
-            for (int nj = 0; nj < 4; ++nj) mma16816(acc[nj], af, bf[nj][0], bf[nj][1]);
-        }
-        __syncthreads();
-    }
-#pragma unroll
-    for (int nj = 0; nj < 4; ++nj)
-#pragma unroll
-        for (int hrow = 0; hrow < 2; ++hrow) {
-            const int co = co0 + warp * 16 + (lane >> 2) + hrow * 8;
-            const int ci = ci0 + nj * 8 + (lane & 3) * 2;
-            if (co >= a.cout) continue;
-            float *d = a.dw + ((long)co * 9 + tap) * a.cin + ci;
-            atomicAdd(d, acc[nj][hrow * 2 + 0]);
-            atomicAdd(d + 1, acc[nj][hrow * 2 + 1]);
-        }
+// Weight gradient on the tcgen05 tensor cores: for one tap and a slice of
+// 128 output channels (M) x BN input channels (N), a block adds up
+// dW[co][tap][ci] = sum_p dz[p][co] x[p + shift][ci] over a pixel range (K)
+// into a tensor-memory accumulator, then adds it to dw with FP32 atomics.
+// Both operands are stored pixel-major (channels contiguous), which is the
+// MN-major canonical layout without swizzle: a core matrix is 8 pixels (K) x
+// 16 bytes (8 channels, MN) = 128 contiguous bytes, so every 16-byte chunk (8
+// channels of one pixel) is staged by cp.async straight into place.  Within
+// a group of 8 channels the 64 pixels of a stage are contiguous (K groups 128
+// bytes apart: the leading byte offset); the groups are 1024 bytes apart (the
+// stride byte offset).  The instruction descriptor marks A and B as MN-major.
+//
+// Only the GA = min(16, cout / 8) channel groups of dz that exist are staged
+// (4 for 32 output channels): the MMA's other A rows read whatever lies
+// beyond the stage (later stages, the B tiles, a pad at the end of shared
+// memory) and only make accumulator rows that are never stored, so the small
+// layers take a quarter of the shared memory and fit more blocks per SM.
+// Every thread stages the same channel group of fixed pixels of each stage,
+// so its source pointers advance by constants; which of a stage's 64 pixels
+// exist (ragged tail) and have the tap's neighbour inside the image is one
+// 64-bit mask per stage, built by every warp with two ballots.  The loads run
+// NS - 2 stages ahead of the MMAs and refill the buffer whose MMAs were
+// issued two steps before; one block barrier per step, which also carries
+// the decision after a wait that ran out (waits are bounded as in
+// conv3x3_kernel).
+constexpr int kWgBK = 64;  // pixels per stage
+__host__ __device__ constexpr int wgrad_groups(int cout) { return cout / 8 < 16 ? cout / 8 : 16; }
+__host__ __device__ constexpr int wgrad_b_bytes(int bn) { return bn * kWgBK * 2; }
+__host__ __device__ constexpr int wgrad_stage_bytes(int bn, int ga) { return ga * kWgBK * 16 + wgrad_b_bytes(bn); }
+// stages: 6 when six fit in 100 KB of shared memory (two or more blocks per SM), else 4
+__host__ __device__ constexpr int wgrad_stages(int bn, int ga) { return 6 * wgrad_stage_bytes(bn, ga) <= 100 * 1024 ? 6 : 4; }
+// mbarriers and the tensor-memory address (128 bytes), the stages, then the
+// pad that the last A stage's unstaged rows may reach into
+__host__ __device__ constexpr int wgrad_tc_smem_bytes(int bn, int ga) {
+    return 128 + wgrad_stages(bn, ga) * wgrad_stage_bytes(bn, ga) +
+           ((16 - ga) * kWgBK * 16 > wgrad_stages(bn, ga) * wgrad_b_bytes(bn)
+                ? (16 - ga) * kWgBK * 16 - wgrad_stages(bn, ga) * wgrad_b_bytes(bn)
+                : 0);
 }
 
-// Weight gradient on the tcgen05 tensor cores: for one tap and a slice of
-// 128 output channels (M, padded with zero rows) x BN input channels (N), a
-// block adds up dW[co][tap][ci] = sum_p dz[p][co] x[p + shift][ci] over a pixel
-// range (K) into a tensor-memory accumulator, then adds it to dw with FP32
-// atomics.  Both operands are stored pixel-major (channels contiguous), which
-// is the MN-major canonical layout without swizzle: a core matrix is 8 pixels
-// (K) x 16 bytes (8 channels, MN) = 128 contiguous bytes, so every 16-byte
-// chunk (8 channels of one pixel) is staged by cp.async straight into place:
-// K groups of 8 pixels 128 bytes apart (leading byte offset), MN groups of 8
-// channels 512 bytes apart (stride byte offset), 32 pixels per stage.  The
-// instruction descriptor marks A and B as MN-major.  Waits are bounded as in
-// conv3x3_kernel.
-__host__ __device__ constexpr int wgrad_tc_smem_bytes(int bn) { return 2 * (128 + bn) * 32 * 2 + 32; }
-
-template <int BN>
+template <int BN, int GA>
 __global__ void __launch_bounds__(128) wgrad3x3_tc_kernel(WgradArgs a, int *err) {
     extern __shared__ __align__(1024) unsigned char sm[];
-    constexpr int BM = 128, BK = 32;
-    constexpr int A_BYTES = BM * BK * 2, B_BYTES = BN * BK * 2;
-    unsigned char *sA = sm, *sB = sm + 2 * A_BYTES;
-    uint64_t *bar = reinterpret_cast<uint64_t *>(sm + 2 * (A_BYTES + B_BYTES));
-    uint32_t *s_taddr = reinterpret_cast<uint32_t *>(bar + 2);
+    constexpr int BM = 128, BK = kWgBK, NS = wgrad_stages(BN, GA);
+    constexpr int A_BYTES = GA * BK * 16, B_BYTES = wgrad_b_bytes(BN);
+    constexpr int BG = BN / 8;             // channel groups of x
+    constexpr int QA = GA * BK / 128;      // A chunks per thread and stage
+    constexpr int QB = BG * BK / 128;      // B chunks per thread and stage
+    static_assert(GA >= 2 && GA <= 16 && 128 % GA == 0 && 128 % BG == 0, "channel groups");
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sm);
+    uint32_t *s_taddr = reinterpret_cast<uint32_t *>(sm + 8 * NS);
+    unsigned char *sA = sm + 128, *sB = sA + NS * A_BYTES;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const long P = (long)a.n * a.h * a.wd;
     const int co0 = blockIdx.x * BM;
@@ -415,89 +359,127 @@ __global__ void __launch_bounds__(128) wgrad3x3_tc_kernel(WgradArgs a, int *err)
     const int dy = tap / 3 - 1, dx = tap % 3 - 1;
     const long pbeg = (long)blockIdx.z * a.pix_per_block;
     const long pend = pbeg + a.pix_per_block < P ? pbeg + a.pix_per_block : P;
-    const int nk = (int)((pend - pbeg + BK - 1) / BK);
+    const int nk = pend > pbeg ? (int)((pend - pbeg + BK - 1) / BK) : 0;
     if (warp == 0) tc::tmem_alloc(s_taddr, BN);
-    if (tid < 2) tc::mbar_init(&bar[tid], 1);
+    if (tid < NS) tc::mbar_init(&bar[tid], 1);
     tc::fence_barrier_init();
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t taddr = *s_taddr;
+    // A: this thread stages group tid % GA of pixels tid / GA + q 128 / GA;
+    // B: group tid % BG of pixels tid / BG + q 128 / BG (consecutive threads
+    // read consecutive 16 bytes of a pixel's channels)
+    const int cga = tid % GA, pxa = tid / GA, cgb = tid % BG, pxb = tid / BG;
+    const bool a_real = co0 + cga * 8 < a.cout;  // channel group inside dz
+    const long stepA = (long)(128 / GA) * a.ld_dz, stepB = (long)(128 / BG) * a.ld_x;
+    const __nv_bfloat16 *srcA = a.dz + (pbeg + pxa) * a.ld_dz + a.coff_dz + co0 + cga * 8;
+    const __nv_bfloat16 *srcB = a.x + (pbeg + pxb + (long)dy * a.wd + dx) * a.ld_x + a.coff_x + ci0 + cgb * 8;
+    const uint32_t dstA = smem_u32(sA) + cga * (BK * 16) + pxa * 16;
+    const uint32_t dstB = smem_u32(sB) + cgb * (BK * 16) + pxb * 16;
+    // image coordinates (column, row) of the first pixel of the next stage to load
+    int sx = (int)(pbeg % a.wd), sy = (int)((pbeg / a.wd) % a.h);
     auto load_stage = [&](int ks, int buf) {
         const long pb = pbeg + (long)ks * BK;
-        unsigned char *A = sA + buf * A_BYTES;
-        unsigned char *B = sB + buf * B_BYTES;
+        // bit i: pixel pb + i exists (tail) / and its tap neighbour is in the image
+        bool e0, e1, v0, v1;
+        {
+            const int i0 = lane, i1 = lane + 32;
+            e0 = pb + i0 < pend;
+            e1 = pb + i1 < pend;
+            int x = sx + i0, y = sy;
+            while (x >= a.wd) {
+                x -= a.wd;
+                ++y;
+            }
+            while (y >= a.h) y -= a.h;
+            v0 = e0 && (unsigned)(y + dy) < (unsigned)a.h && (unsigned)(x + dx) < (unsigned)a.wd;
+            x = sx + i1;
+            y = sy;
+            while (x >= a.wd) {
+                x -= a.wd;
+                ++y;
+            }
+            while (y >= a.h) y -= a.h;
+            v1 = e1 && (unsigned)(y + dy) < (unsigned)a.h && (unsigned)(x + dx) < (unsigned)a.wd;
+        }
+        const uint64_t em = (uint64_t)__ballot_sync(0xffffffffu, e0) | ((uint64_t)__ballot_sync(0xffffffffu, e1) << 32);
+        const uint64_t vm = (uint64_t)__ballot_sync(0xffffffffu, v0) | ((uint64_t)__ballot_sync(0xffffffffu, v1) << 32);
+        const long off = (long)ks * BK;
+        const __nv_bfloat16 *gA = srcA + off * a.ld_dz;
+        const __nv_bfloat16 *gB = srcB + off * a.ld_x;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {  // A: 32 pixels x 16 groups of 8 output channels
-            const int idx = tid + q * 128;
-            const int px = idx >> 4, cg = idx & 15;
-            const long p = pb + px;
-            const bool ok = p < pend && co0 + cg * 8 < a.cout;
-            const __nv_bfloat16 *g = a.dz + (ok ? p : 0) * a.ld_dz + a.coff_dz + (ok ? co0 + cg * 8 : 0);
-            cp_async16(A + cg * 512 + (px >> 3) * 128 + (px & 7) * 16, g, ok);
+        for (int q = 0; q < QA; ++q) {
+            const bool ok = a_real && ((em >> (pxa + q * (128 / GA))) & 1);
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dstA + buf * A_BYTES +
+                                                                              q * (128 / GA) * 16),
+                         "l"(ok ? gA + q * stepA : a.dz), "r"(ok ? 16 : 0));
         }
 #pragma unroll
-        for (int q = 0; q < BN / 32; ++q) {  // B: 32 pixels x BN/8 groups of 8 input channels
-            const int idx = tid + q * 128;
-            const int px = idx / (BN / 8), cg = idx % (BN / 8);
-            const long p = pb + px;
-            bool ok = p < pend;
-            long src = 0;
-            if (ok) {
-                const int xq = (int)(p % a.wd);
-                const int yq = (int)((p / a.wd) % a.h);
-                ok = yq + dy >= 0 && yq + dy < a.h && xq + dx >= 0 && xq + dx < a.wd;
-                src = p + (long)dy * a.wd + dx;
-            }
-            const __nv_bfloat16 *g = a.x + (ok ? src : 0) * a.ld_x + a.coff_x + ci0 + cg * 8;
-            cp_async16(B + cg * 512 + (px >> 3) * 128 + (px & 7) * 16, g, ok);
+        for (int q = 0; q < QB; ++q) {
+            const bool ok = (vm >> (pxb + q * (128 / BG))) & 1;
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dstB + buf * B_BYTES +
+                                                                              q * (128 / BG) * 16),
+                         "l"(ok ? gB + q * stepB : a.x), "r"(ok ? 16 : 0));
         }
         cp_async_commit();
+        sx += BK;
+        while (sx >= a.wd) {
+            sx -= a.wd;
+            ++sy;
+        }
+        while (sy >= a.h) sy -= a.h;
     };
     constexpr uint32_t idesc = tc::idesc_bf16(BM, BN) | (1u << 15) | (1u << 16);  // A and B MN-major
+    // stage ks lives in buffer ks % NS; the n-th use of a buffer (n = ks / NS)
+    // completes its mbarrier's phase n, of parity n & 1
     bool ok = true;
     int last = -1;  // last K step whose MMAs were committed
-    if (nk > 0) load_stage(0, 0);
+    for (int s = 0; s < NS - 2; ++s) {  // prologue: NS - 2 stages in flight (empty groups past the end)
+        if (s < nk) load_stage(s, s);
+        else cp_async_commit();
+    }
     for (int ks = 0; ks < nk; ++ks) {
-        const int buf = ks & 1;
-        if (ks + 1 < nk) {
-            if (ks >= 1) ok = tc::mbar_wait(&bar[buf ^ 1], ((ks - 1) >> 1) & 1);
-            if (!__syncthreads_and(ok)) {
-                ok = false;
-                break;
-            }
-            load_stage(ks + 1, buf ^ 1);
-            cp_async_wait<1>();
-        } else {
-            cp_async_wait<0>();
-        }
+        const int buf = ks % NS;
+        cp_async_wait<NS - 3>();  // stage ks has landed (this thread's copies)
         tc::fence_proxy_async();
-        __syncthreads();
+        // one decision for the whole block: after a wait that ran out, no
+        // thread issues MMAs or overwrites a stage the tensor cores could read
+        if (!__syncthreads_and(ok)) {
+            ok = false;
+            break;
+        }
         if (tid == 0) {
             tc::fence_after_sync();
             const unsigned char *A = sA + buf * A_BYTES, *B = sB + buf * B_BYTES;
 #pragma unroll
             for (int kh = 0; kh < BK / 16; ++kh)  // 16 pixels (two K groups) per MMA
-                tc::mma_bf16(taddr, tc::smem_desc(A + kh * 256, 128, 512), tc::smem_desc(B + kh * 256, 128, 512),
-                             idesc, (ks > 0 || kh > 0) ? 1u : 0u);
+                tc::mma_bf16(taddr, tc::smem_desc(A + kh * 256, 128, BK * 16),
+                             tc::smem_desc(B + kh * 256, 128, BK * 16), idesc, (ks > 0 || kh > 0) ? 1u : 0u);
             tc::mma_commit(&bar[buf]);
         }
         last = ks;
+        // refill the buffer of stage ks - 2 with stage ks + NS - 2 once its MMAs
+        // are done (issued two steps earlier, so the wait is normally over)
+        const int nxt = ks + NS - 2;
+        if (nxt < nk && ks >= 2) ok = tc::mbar_wait(&bar[(ks - 2) % NS], ((ks - 2) / NS) & 1);
+        if (nxt < nk && ok) load_stage(nxt, nxt % NS);
+        else cp_async_commit();  // keep one group per step for the wait count
     }
-    if (ok && nk > 0) ok = tc::mbar_wait(&bar[(nk - 1) & 1], ((nk - 1) >> 1) & 1);
+    if (ok && nk > 0) ok = tc::mbar_wait(&bar[(nk - 1) % NS], ((nk - 1) / NS) & 1);
     if (!__syncthreads_and(ok)) {
         // a wait ran out: flag, let the copies land, one more bounded wait for
         // the committed MMAs, release the tensor memory, add nothing
         if (tid == 0) atomicOr(err, 1);
         cp_async_wait<0>();
-        if (last >= 0) tc::mbar_wait(&bar[last & 1], (last >> 1) & 1);
+        if (last >= 0) tc::mbar_wait(&bar[last % NS], (last / NS) & 1);
         tc::fence_before_sync();
         __syncthreads();
         if (warp == 0) tc::tmem_dealloc(taddr, BN);
         return;
     }
     tc::fence_after_sync();
-    if (nk > 0) {
+    if (nk > 0 && co0 + warp * 32 < a.cout) {  // warps whose rows are all padding skip the epilogue
         const int co = co0 + warp * 32 + lane;  // this thread's accumulator row (tensor-memory lane)
 #pragma unroll 1
         for (int c = 0; c < BN; c += 8) {
