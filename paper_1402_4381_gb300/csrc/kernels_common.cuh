@@ -161,6 +161,25 @@ __device__ __forceinline__ void finish_subset_iteration(const UpdateArgs &ua, in
     double v = 0.0, vy = 0.0, vd = 0.0;
     const int nt = blockDim.x * blockDim.y * blockDim.z;
     const int tid = (threadIdx.z * blockDim.y + threadIdx.y) * blockDim.x + threadIdx.x;
+    DevState *st = ua.state;
+    // thread 0 fetches the state and the two continuation-table entries the
+    // update may need (l + 1, or 0 after a restart) before the partials, so
+    // their latency overlaps the reduction
+    double rho_used = 0.0, alpha = 1.0;
+    int j = 0, l = 0;
+    bool tab = false;
+    RhoEnt e0{}, e1{};
+    if (tid == 0) {
+        rho_used = __ldcg(&st->rho);
+        alpha = __ldcg(&st->alpha);
+        j = __ldcg(&st->j);
+        l = __ldcg(&st->l);
+        tab = ua.rho_mode != OSLALM_RHO_FIXED && ua.rho_tab && l + 1 < ua.rho_tab_n;
+        if (tab) {
+            e0 = ua.rho_tab[0];
+            e1 = ua.rho_tab[l + 1];
+        }
+    }
     for (int i = tid; i < nblocks; i += nt) {
         v += __ldcg(ua.partials + i);
         if (ua.bb) {
@@ -174,11 +193,7 @@ __device__ __forceinline__ void finish_subset_iteration(const UpdateArgs &ua, in
         vd = block_sum2d(vd, red_last);
     }
     if (tid == 0) {
-        DevState *st = ua.state;
         const double xi = v;
-        const double rho_used = st->rho;
-        const int j = st->j;
-        int l = st->l;
         int restart = 0;
         double rho = rho_used;
         if (ua.rho_mode == OSLALM_RHO_CONTINUATION) {
@@ -186,10 +201,9 @@ __device__ __forceinline__ void finish_subset_iteration(const UpdateArgs &ua, in
         } else if (ua.rho_mode == OSLALM_RHO_REPLAY) {
             restart = (ua.replay && j < ua.replay_n) ? (ua.replay[j] != 0) : 0;
         }
-        const bool tab = ua.rho_mode != OSLALM_RHO_FIXED && ua.rho_tab && l + 1 < ua.rho_tab_n;
         if (ua.rho_mode != OSLALM_RHO_FIXED) {
             l = restart ? 0 : l + 1;
-            rho = tab ? ua.rho_tab[l].rho : rho_of_l(l, ua.rho_min);
+            rho = tab ? (restart ? e0.rho : e1.rho) : rho_of_l(l, ua.rho_min);
         }
         if (ua.bb) {  // refit H = alpha D at the end of every iteration
             st->bb_num += vy;
@@ -197,7 +211,8 @@ __device__ __forceinline__ void finish_subset_iteration(const UpdateArgs &ua, in
             ua.bbhave[ua.subset] = 1;
             if ((j + 1) % ua.M == 0) {
                 const double num = st->bb_num, den = st->bb_den;
-                st->alpha = (den > 0.0 && num > 0.0) ? fmin(num / den, 1.0) : 1.0;
+                alpha = (den > 0.0 && num > 0.0) ? fmin(num / den, 1.0) : 1.0;
+                st->alpha = alpha;
                 st->bb_num = 0.0;
                 st->bb_den = 0.0;
             }
@@ -206,10 +221,11 @@ __device__ __forceinline__ void finish_subset_iteration(const UpdateArgs &ua, in
         st->l = l;
         st->rho = rho;
         if (tab) {  // the same values refresh_rho_factors forms, from the host's table
+            const RhoEnt &e = restart ? e0 : e1;
             st->rho_f = (float)rho;
-            st->rho_d_f = st->alpha == 1.0 ? st->rho_f : (float)(rho * st->alpha);
-            st->ga = ua.rho_tab[l].ga;
-            st->gb = ua.rho_tab[l].gb;
+            st->rho_d_f = alpha == 1.0 ? (float)rho : (float)(rho * alpha);
+            st->ga = e.ga;
+            st->gb = e.gb;
         } else if (ua.rho_mode != OSLALM_RHO_FIXED || ua.bb) {
             refresh_rho_factors(st);
         }
@@ -221,12 +237,11 @@ __device__ __forceinline__ void finish_subset_iteration(const UpdateArgs &ua, in
             rec.restart = restart;
             rec.subset = ua.subset;
             rec.pad = 0;
-            rec.alpha = st->alpha;
+            rec.alpha = alpha;
             ua.stats[j % ua.stats_cap] = rec;
         }
         st->j = j + 1;
-        st->counter = 0;
-        __threadfence();
+        st->counter = 0;  // read by the next launch (kernel boundaries order it)
     }
 }
 

@@ -291,17 +291,26 @@ __device__ __forceinline__ void update_tile(float *tile, int ix0, int iy0, int t
                                             const float *__restrict__ zeta, const float *__restrict__ gs,
                                             const DT *__restrict__ D, const float *__restrict__ dscale, float rho,
                                             float rho_d, float beta, float inv_delta, int curv_mode) {
-    load_tile_halo<TX, TY>(tile, ix0, iy0, tid, nthreads, nx, ny, x);
     const int ix = ix0 + tx, iy = iy0 + ty;
-    if (ix < nx && iy < ny) {
+    const bool in = ix < nx && iy < ny;
+    const size_t p = in ? (size_t)iy * nx + ix : 0;
+    // this pixel's zeta, g and D are loaded before the tile's barrier, so
+    // their latency overlaps the halo load
+    float z = 0.f, g = 0.f, d = 0.f;
+    if (in) {
+        z = __ldg(zeta + p);
+        g = __ldg(gs + p);
+        d = load_w(D, p);
+    }
+    load_tile_halo<TX, TY>(tile, ix0, iy0, tid, nthreads, nx, ny, x);
+    if (in) {
         const float xj = tile[(ty + 1) * (TX + 2) + tx + 1];
         float grad, curv;
         stencil2d<TX, NBR>(tile, tx, ty, ix, iy, nx, ny, inv_delta, curv_mode, grad, curv);
         grad *= beta;
         curv *= 2.f * beta;
-        const size_t p = (size_t)iy * nx + ix;
-        const float s = rho * __ldg(zeta + p) + (1.f - rho) * __ldg(gs + p);
-        const float den = rho_d * (load_w(D, p) * __ldg(dscale)) + curv;
+        const float s = rho * z + (1.f - rho) * g;
+        const float den = rho_d * (d * __ldg(dscale)) + curv;
         const float xn = den > 0.f ? xj - (s + grad) / den : xj;  // no curvature: unchanged
         xo[p] = fmaxf(xn, 0.f);
     }
