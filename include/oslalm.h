@@ -349,7 +349,12 @@ int oslalm_batch_shape_info(int shape, int *tile_x, int *tile_y, int *lanes);
  * oslalm_cnn_mark_timeout: sets that mark from the host, exactly as a
  *   convolution whose wait ran out would (synchronous), so that callers can
  *   test their handling of OSLALM_ERR_TIMEOUT without a device fault.
- *   Errors: ARG, CUDA. */
+ *   Errors: ARG, CUDA.
+ * oslalm_cnn_set_tma: enable (default) or disable the TMA convolution, used
+ *   where a level's 128-pixel blocks are whole rows or row segments (width a
+ *   multiple of 128, or 128 / width rows with the height a multiple of that);
+ *   disabled, every convolution stages its tiles with cp.async.  Both run
+ *   the same MMAs in the same order, so the results are identical.  Errors: ARG. */
 typedef struct oslalm_cnn oslalm_cnn;
 long oslalm_cnn_param_count(void);
 int oslalm_cnn_create(int batch, int height, int width, unsigned long long seed, oslalm_cnn **out);
@@ -363,6 +368,7 @@ int oslalm_cnn_train_step(oslalm_cnn *c, const float *x, const float *target, in
                           double *loss, void *stream);
 double oslalm_cnn_flops_per_image(int height, int width);
 int oslalm_cnn_mark_timeout(oslalm_cnn *c);
+int oslalm_cnn_set_tma(oslalm_cnn *c, int enable);
 
 /* ---- monitoring ----------------------------------------------------------
  * *out[host] = sqrt(sum_{mask} (x - xref)^2 / count(mask)) over the pixels

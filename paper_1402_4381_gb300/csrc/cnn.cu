@@ -10,6 +10,8 @@
 #include <new>
 #include <vector>
 
+#include <cudaTypedefs.h>
+
 #include "cnn_kernels.cuh"
 #include "common.cuh"
 #include "kernels_common.cuh"
@@ -246,6 +248,7 @@ struct oslalm_cnn {
     float *w32 = nullptr, *grad = nullptr, *m = nullptr, *v = nullptr;
     __nv_bfloat16 *wb[NL] = {}, *wt[NL] = {};
     long step = 0;
+    int use_tma = 1;  // convolutions whose blocks are whole rows take their tiles by TMA
     // activations (BF16 NHWC)
     __nv_bfloat16 *in0 = nullptr, *e0a = nullptr, *cat0 = nullptr, *p0 = nullptr, *e1a = nullptr, *cat1 = nullptr,
                   *p1 = nullptr, *e2a = nullptr, *cat2 = nullptr, *p2 = nullptr, *b3a = nullptr, *b3b = nullptr,
@@ -260,6 +263,62 @@ struct oslalm_cnn {
 };
 
 namespace {
+
+// cuTensorMapEncodeTiled of the driver, looked up once through the runtime
+// (null if the driver does not provide it)
+PFN_cuTensorMapEncodeTiled_v12000 encode_tiled() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool looked = false;
+    if (!looked) {
+        looked = true;
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+
+// Tensor maps of the TMA convolution: the input slice as (channel, column,
+// row, image) with boxes of 8 channels x bw x bh, the weights [cout][9 cin]
+// with boxes of 8 x bn.  False if the geometry or the alignment does not allow it.
+bool conv_tensor_maps(const __nv_bfloat16 *in, int ld_in, int coff_in, int cin, const __nv_bfloat16 *w, int cout,
+                      int n, int h, int wd, int bn, CUtensorMap *ta, CUtensorMap *tb) {
+    int bw = 0, bh = 0;  // a block's 128 pixels: a row segment, or 128 / wd whole rows
+    if (wd % kBM == 0) {
+        bw = kBM;
+        bh = 1;
+    } else if (kBM % wd == 0 && h % (kBM / wd) == 0) {
+        bw = wd;
+        bh = kBM / wd;
+    } else {
+        return false;
+    }
+    const __nv_bfloat16 *base = in + coff_in;
+    if (reinterpret_cast<uintptr_t>(base) % 16 || reinterpret_cast<uintptr_t>(w) % 16 || ld_in % 8 || cin % 8)
+        return false;
+    PFN_cuTensorMapEncodeTiled_v12000 enc = encode_tiled();
+    if (!enc) return false;
+    const cuuint64_t es = 2;  // bytes per BF16
+    const cuuint64_t gdA[4] = {(cuuint64_t)cin, (cuuint64_t)wd, (cuuint64_t)h, (cuuint64_t)n};
+    const cuuint64_t gsA[3] = {ld_in * es, (cuuint64_t)wd * ld_in * es, (cuuint64_t)h * wd * ld_in * es};
+    const cuuint32_t boxA[4] = {8, (cuuint32_t)bw, (cuuint32_t)bh, 1};
+    const cuuint32_t one[4] = {1, 1, 1, 1};
+    if (enc(ta, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<__nv_bfloat16 *>(base), gdA, gsA, boxA, one,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return false;
+    const cuuint64_t gdB[2] = {(cuuint64_t)9 * cin, (cuuint64_t)cout};
+    const cuuint64_t gsB[1] = {(cuuint64_t)9 * cin * es};
+    const cuuint32_t boxB[2] = {8, (cuuint32_t)bn};
+    return enc(tb, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16 *>(w), gdB, gsB, boxB, one,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
 
 int conv(const oslalm_cnn *c, const __nv_bfloat16 *in, int ld_in, int coff_in, int cin, const __nv_bfloat16 *w,
          const float *bias, __nv_bfloat16 *out, int ld_out, int coff_out, int cout, int n, int h, int wd, int relu,
@@ -276,6 +335,28 @@ int conv(const oslalm_cnn *c, const __nv_bfloat16 *in, int ld_in, int coff_in, i
     while (cout % bn) bn >>= 1;
     if (bn < 32 || cin % kBK) return fail(OSLALM_ERR_ARG, "convolution needs channel counts that are multiples of 32");
     dim3 grid(nb(P, kBM), cout / bn);
+    CUtensorMap ta, tb;
+    if (c->use_tma && conv_tensor_maps(in, ld_in, coff_in, cin, w, cout, n, h, wd, bn, &ta, &tb)) {
+#define OSL_CONV_TMA(BN)                                                                                   \
+    do {                                                                                                   \
+        static bool opted = false;                                                                         \
+        if (!opted) {                                                                                      \
+            OSL_CUDA_TRY(cudaFuncSetAttribute(conv3x3_tma_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                              conv_tma_smem_bytes(BN)));                                   \
+            opted = true;                                                                                  \
+        }                                                                                                  \
+        conv3x3_tma_kernel<BN><<<grid, 128, conv_tma_smem_bytes(BN), st>>>(ta, tb, a, c->err);            \
+    } while (0)
+        switch (bn) {
+            case 32: OSL_CONV_TMA(32); break;
+            case 64: OSL_CONV_TMA(64); break;
+            case 128: OSL_CONV_TMA(128); break;
+            default: OSL_CONV_TMA(256); break;
+        }
+#undef OSL_CONV_TMA
+        OSL_LAUNCH_CHECK("conv3x3_tma_kernel");
+        return OSLALM_OK;
+    }
 #define OSL_CONV(BN)                                                                                       \
     do {                                                                                                   \
         static bool opted = false; /* dynamic shared memory above 48 KB, once */                          \
@@ -640,6 +721,13 @@ int oslalm_cnn_destroy(oslalm_cnn *c) {
     if (!c) return OSLALM_OK;
     for (void *p : c->allocs) cudaFree(p);
     delete c;
+    return OSLALM_OK;
+}
+
+int oslalm_cnn_set_tma(oslalm_cnn *c, int enable) {
+    clear_error();
+    if (!c) return fail(OSLALM_ERR_ARG, "network handle is NULL");
+    c->use_tma = enable != 0;
     return OSLALM_OK;
 }
 

@@ -16,6 +16,7 @@
 //   added with FP32 atomics.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <stdint.h>
 
@@ -150,6 +151,37 @@ constexpr int kBM = 128, kBK = 32;  // pixels per block; input channels (one tap
 // B (BN x 32) tiles, then two mbarriers and the tensor-memory address
 __host__ __device__ constexpr int conv_smem_bytes(int bn) { return 2 * (kBM + bn) * kBK * 2 + 32; }
 
+// Epilogue of a 128-pixel x BN tile: thread = pixel (tensor-memory lane),
+// bias, ReLU, BF16 stores of 8 channels at a time.
+template <int BN>
+__device__ __forceinline__ void conv_epilogue(const ConvArgs &a, uint32_t taddr, long p0, int co0, long P) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const long p = p0 + warp * 32 + lane;  // this thread's accumulator row (tensor-memory lane)
+#pragma unroll 1
+    for (int c = 0; c < BN; c += 8) {
+        float v[8];
+        tc::tmem_ld8(taddr + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, v);
+        if (p < P) {
+            const int co = co0 + c;
+            __align__(16) __nv_bfloat162 o[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                float v0 = v[2 * i], v1 = v[2 * i + 1];
+                if (a.bias) {
+                    v0 += a.bias[co + 2 * i];
+                    v1 += a.bias[co + 2 * i + 1];
+                }
+                if (a.relu) {
+                    v0 = fmaxf(v0, 0.f);
+                    v1 = fmaxf(v1, 0.f);
+                }
+                o[i] = __floats2bfloat162_rn(v0, v1);
+            }
+            *reinterpret_cast<uint4 *>(a.out + p * a.ld_out + a.coff_out + co) = *reinterpret_cast<const uint4 *>(o);
+        }
+    }
+}
+
 // One block: 128 pixels x BN output channels.  Every K step (one tap x 32 input
 // channels) is staged by all threads with cp.async into the core-matrix
 // layout (zero rows outside the image), then one thread issues two
@@ -166,7 +198,7 @@ __global__ void __launch_bounds__(128) conv3x3_kernel(ConvArgs a, int *err) {
     unsigned char *sA = sm, *sB = sm + 2 * A_BYTES;
     uint64_t *bar = reinterpret_cast<uint64_t *>(sm + 2 * (A_BYTES + B_BYTES));
     uint32_t *s_taddr = reinterpret_cast<uint32_t *>(bar + 2);
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tid = threadIdx.x, warp = tid >> 5;
     const long P = (long)a.n * a.h * a.wd;
     const long p0 = (long)blockIdx.x * kBM;
     const int co0 = blockIdx.y * BN;
@@ -260,30 +292,154 @@ __global__ void __launch_bounds__(128) conv3x3_kernel(ConvArgs a, int *err) {
         return;
     }
     tc::fence_after_sync();
-    const long p = p0 + warp * 32 + lane;  // this thread's accumulator row (tensor-memory lane)
-#pragma unroll 1
-    for (int c = 0; c < BN; c += 8) {
-        float v[8];
-        tc::tmem_ld8(taddr + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, v);
-        if (p < P) {
-            const int co = co0 + c;
-            __align__(16) __nv_bfloat162 o[4];
+    conv_epilogue<BN>(a, taddr, p0, co0, P);
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(taddr, BN);
+}
+
+// ---------------------------------------------------------------- TMA (tensor memory accelerator)
+namespace tma {
+__device__ __forceinline__ void prefetch_map(const CUtensorMap *m) {
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(m)) : "memory");
+}
+// one arrival on `bar` that also expects `bytes` of TMA transfers in this phase
+__device__ __forceinline__ void arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+// box of a rank-4 / rank-2 tensor map at the given element coordinates (the
+// innermost first) into shared memory; elements outside the tensor read as zero
+__device__ __forceinline__ void load_4d(void *dst, const CUtensorMap *m, int c0, int c1, int c2, int c3,
+                                        uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+        "%5}], [%6];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(m)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void load_2d(void *dst, const CUtensorMap *m, int c0, int c1, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+        "[%4];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(m)), "r"(c0), "r"(c1), "r"(smem_u32(bar))
+        : "memory");
+}
+}  // namespace tma
+
+constexpr int kConvTmaStages = 4;
+// barriers + tensor-memory address (128 bytes), then the stages: A (128
+// pixels x 32 channels) and B (BN output channels x 32 channels)
+__host__ __device__ constexpr int conv_tma_smem_bytes(int bn) { return 128 + kConvTmaStages * (kBM + bn) * kBK * 2; }
+
+// The convolution with its operand tiles brought in by TMA, for images whose
+// 128-pixel blocks are whole rows or row segments (width a multiple of 128,
+// or 128 / width rows with the height a multiple of that).  The activations
+// are a rank-4 tensor map (channel, column, row, image) over the input
+// slice: the tile of tap (dy, dx) is the box of 8 channels x bw columns x bh
+// rows at (ci, x0 + dx, y0 + dy, image), and the map's zero fill outside the
+// image is the convolution's zero padding.  Each box lands as 128 pixels x 16
+// bytes, the K-major core-matrix layout with 8-pixel groups 128 bytes apart
+// (stride byte offset) and 8-channel groups 2048 bytes apart (leading byte
+// offset); the weights [cout][9 cin] are a rank-2 map read the same way.  One
+// thread runs the whole loop: it keeps all four stages in flight, waits for a
+// stage's bytes on its `full` mbarrier, issues the two MMAs, commits them to
+// the stage's `empty` mbarrier and refills the stage used one step earlier
+// once those MMAs are done.  The other threads wait for the epilogue.  Waits
+// are bounded; after one runs out the block lets its transfers land and its
+// MMAs finish (bounded), flags err, releases the tensor memory and returns.
+template <int BN>
+__global__ void __launch_bounds__(128) conv3x3_tma_kernel(const __grid_constant__ CUtensorMap tmA,
+                                                          const __grid_constant__ CUtensorMap tmB, ConvArgs a,
+                                                          int *err) {
+    extern __shared__ __align__(1024) unsigned char sm[];
+    constexpr int NS = kConvTmaStages;
+    constexpr int A_BYTES = kBM * kBK * 2, B_BYTES = BN * kBK * 2, S_BYTES = A_BYTES + B_BYTES;
+    uint64_t *full = reinterpret_cast<uint64_t *>(sm);
+    uint64_t *empty = full + NS;
+    uint32_t *s_taddr = reinterpret_cast<uint32_t *>(empty + NS);
+    unsigned char *stages = sm + 128;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const long P = (long)a.n * a.h * a.wd;
+    const long p0 = (long)blockIdx.x * kBM;
+    const int co0 = blockIdx.y * BN;
+    const int csteps = a.cin / kBK;
+    const int nk = 9 * csteps;
+    if (warp == 0) tc::tmem_alloc(s_taddr, BN);
+    if (tid < 2 * NS) tc::mbar_init(&full[tid], 1);  // full[0..NS) and empty[0..NS)
+    tc::fence_barrier_init();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t taddr = *s_taddr;
+    bool ok = true;
+    if (tid == 0) {
+        tma::prefetch_map(&tmA);
+        tma::prefetch_map(&tmB);
+        const long hw = (long)a.h * a.wd;
+        const int img = (int)(p0 / hw);
+        const int rem = (int)(p0 - (long)img * hw);
+        const int y0 = rem / a.wd, x0 = rem - (rem / a.wd) * a.wd;
+        int issued = 0, done = 0;
+        int tap_i = 0, cs_i = 0;  // tap and channel step of the next stage to issue
+        auto issue = [&]() {
+            const int s = issued++;
+            unsigned char *A = stages + (s % NS) * S_BYTES, *B = A + A_BYTES;
+            uint64_t *fb = &full[s % NS];
+            const int dy = tap_i / 3 - 1, dx = tap_i % 3 - 1, ci0 = cs_i * kBK;
+            tma::arrive_expect_tx(fb, (uint32_t)S_BYTES);
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                float v0 = v[2 * i], v1 = v[2 * i + 1];
-                if (a.bias) {
-                    v0 += a.bias[co + 2 * i];
-                    v1 += a.bias[co + 2 * i + 1];
-                }
-                if (a.relu) {
-                    v0 = fmaxf(v0, 0.f);
-                    v1 = fmaxf(v1, 0.f);
-                }
-                o[i] = __floats2bfloat162_rn(v0, v1);
+            for (int g = 0; g < kBK / 8; ++g) tma::load_4d(A + g * (kBM * 16), &tmA, ci0 + 8 * g, x0 + dx, y0 + dy, img, fb);
+#pragma unroll
+            for (int g = 0; g < kBK / 8; ++g) tma::load_2d(B + g * (BN * 16), &tmB, tap_i * a.cin + ci0 + 8 * g, co0, fb);
+            if (++cs_i == csteps) {
+                cs_i = 0;
+                ++tap_i;
             }
-            *reinterpret_cast<uint4 *>(a.out + p * a.ld_out + a.coff_out + co) = *reinterpret_cast<const uint4 *>(o);
+        };
+        while (issued < NS && issued < nk) issue();
+        for (int ks = 0; ks < nk; ++ks) {
+            const int buf = ks % NS;
+            if (!tc::mbar_wait(&full[buf], (ks / NS) & 1)) {
+                ok = false;
+                break;
+            }
+            tc::fence_after_sync();
+            const unsigned char *A = stages + buf * S_BYTES, *B = A + A_BYTES;
+#pragma unroll
+            for (int kh = 0; kh < kBK / 16; ++kh)  // 16 channels (two 8-channel groups) per MMA
+                tc::mma_bf16(taddr, tc::smem_desc(A + kh * 2 * (kBM * 16), kBM * 16, 128),
+                             tc::smem_desc(B + kh * 2 * (BN * 16), BN * 16, 128), tc::idesc_bf16(kBM, BN),
+                             (ks > 0 || kh > 0) ? 1u : 0u);
+            tc::mma_commit(&empty[buf]);
+            done = ks + 1;
+            // refill the stage of step ks - 1: its MMAs precede this step's in
+            // the tensor pipe, so they are normally done
+            if (ks >= 1 && issued < nk) {
+                if (!tc::mbar_wait(&empty[(ks - 1) % NS], ((ks - 1) / NS) & 1)) {
+                    ok = false;
+                    break;
+                }
+                issue();
+            }
+        }
+        if (ok && nk > 0) ok = tc::mbar_wait(&empty[(nk - 1) % NS], ((nk - 1) / NS) & 1);
+        if (!ok) {
+            // let the issued transfers land and the committed MMAs finish
+            // (each wait bounded) before the block's memory is released
+            atomicOr(err, 1);
+            for (int s = done; s < issued; ++s) tc::mbar_wait(&full[s % NS], (s / NS) & 1);
+            if (done > 0) tc::mbar_wait(&empty[(done - 1) % NS], ((done - 1) / NS) & 1);
         }
     }
+    if (!__syncthreads_and(ok)) {
+        tc::fence_before_sync();
+        __syncthreads();
+        if (warp == 0) tc::tmem_dealloc(taddr, BN);
+        return;
+    }
+    tc::fence_after_sync();
+    conv_epilogue<BN>(a, taddr, p0, co0, P);
     tc::fence_before_sync();
     __syncthreads();
     if (warp == 0) tc::tmem_dealloc(taddr, BN);

@@ -188,3 +188,34 @@ def test_timeout_mark_is_reported_once_and_cleared(L):
     assert e.value.code == -4
     assert np.isfinite(net.train_step(x, x, 50.0, 1e-4, want_loss=True))
     net.close()
+
+
+@pytest.mark.parametrize("shape", [(1, 64, 128), (2, 32, 32)])
+def test_tma_and_cp_async_convolutions_agree_bit_for_bit(L, shape):
+    """The TMA convolution (levels whose 128-pixel blocks are whole rows or
+    row segments: all four levels of 64 x 128, the first two of 32 x 32)
+    issues the same MMAs in the same order as the cp.async one, so the
+    network's output must be identical; the loss and the gradients agree to
+    the rounding of their atomic sums (whose order varies from run to run)."""
+    import torch
+    n, h, w = shape
+    rng = np.random.default_rng(11)
+    x = rng.uniform(0, 2, size=shape).astype(np.float32)
+    t = (x + rng.normal(0, 0.3, size=shape)).astype(np.float32)
+    p = _params()
+    xd, td = torch.as_tensor(x, device="cuda"), torch.as_tensor(t, device="cuda")
+    res = []
+    for tma in (True, False):
+        net = L.WarmStartNet(n, h, w, seed=0)
+        net.set_params(L.cnn_flatten(p))
+        net.set_tma(tma)
+        y = net.forward(xd, 1.0).cpu().numpy()
+        loss, g = net.gradients(xd, td, 1.0)
+        res.append((y, loss, g))
+    (y1, l1, g1), (y0, l0, g0) = res
+    assert np.all(np.isfinite(y1)) and np.all(np.isfinite(g1))
+    assert np.array_equal(y1, y0)
+    assert abs(l1 - l0) <= 1e-12 * l0
+    g1d, g0d = L.cnn_unflatten(g1), L.cnn_unflatten(g0)
+    bad = {k: v for k in g0d if not (v := _rel(g1d[k].astype(np.float64), g0d[k].astype(np.float64))) < 1e-5}
+    assert not bad, bad
