@@ -284,8 +284,8 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_tiled() {
 }
 
 // Tensor maps of the TMA convolution: the input slice as (channel, column,
-// row, image) with boxes of 8 channels x bw x bh, the weights [cout][9 cin]
-// with boxes of 8 x bn.  False if the geometry or the alignment does not allow it.
+// row, image) with boxes of 32 channels x bw x bh, the weights [cout][9 cin]
+// with boxes of 32 x bn, both in the 64-byte swizzle.  False if the geometry or the alignment does not allow it.
 bool conv_tensor_maps(const __nv_bfloat16 *in, int ld_in, int coff_in, int cin, const __nv_bfloat16 *w, int cout,
                       int n, int h, int wd, int bn, CUtensorMap *ta, CUtensorMap *tb) {
     int bw = 0, bh = 0;  // a block's 128 pixels: a row segment, or 128 / wd whole rows
@@ -299,24 +299,24 @@ bool conv_tensor_maps(const __nv_bfloat16 *in, int ld_in, int coff_in, int cin, 
         return false;
     }
     const __nv_bfloat16 *base = in + coff_in;
-    if (reinterpret_cast<uintptr_t>(base) % 16 || reinterpret_cast<uintptr_t>(w) % 16 || ld_in % 8 || cin % 8)
+    if (reinterpret_cast<uintptr_t>(base) % 16 || reinterpret_cast<uintptr_t>(w) % 16 || ld_in % 8 || cin % kBK)
         return false;
     PFN_cuTensorMapEncodeTiled_v12000 enc = encode_tiled();
     if (!enc) return false;
     const cuuint64_t es = 2;  // bytes per BF16
     const cuuint64_t gdA[4] = {(cuuint64_t)cin, (cuuint64_t)wd, (cuuint64_t)h, (cuuint64_t)n};
     const cuuint64_t gsA[3] = {ld_in * es, (cuuint64_t)wd * ld_in * es, (cuuint64_t)h * wd * ld_in * es};
-    const cuuint32_t boxA[4] = {8, (cuuint32_t)bw, (cuuint32_t)bh, 1};
+    const cuuint32_t boxA[4] = {(cuuint32_t)kBK, (cuuint32_t)bw, (cuuint32_t)bh, 1};
     const cuuint32_t one[4] = {1, 1, 1, 1};
     if (enc(ta, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<__nv_bfloat16 *>(base), gdA, gsA, boxA, one,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return false;
     const cuuint64_t gdB[2] = {(cuuint64_t)9 * cin, (cuuint64_t)cout};
     const cuuint64_t gsB[1] = {(cuuint64_t)9 * cin * es};
-    const cuuint32_t boxB[2] = {8, (cuuint32_t)bn};
+    const cuuint32_t boxB[2] = {(cuuint32_t)kBK, (cuuint32_t)bn};
     return enc(tb, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16 *>(w), gdB, gsB, boxB, one,
-               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
@@ -552,6 +552,7 @@ int check_waits(oslalm_cnn *c) {
     OSL_CUDA_TRY(cudaMemcpy(&flag, c->err, sizeof(int), cudaMemcpyDeviceToHost));
     if (!flag) return OSLALM_OK;
     OSL_CUDA_TRY(cudaMemset(c->err, 0, sizeof(int)));
+    if (flag & 2) return fail(OSLALM_ERR_CUDA, "TMA convolution found its shared memory misaligned; output invalid");
     return fail(OSLALM_ERR_TIMEOUT, "a convolution's tensor-core wait ran out; its output is invalid");
 }
 

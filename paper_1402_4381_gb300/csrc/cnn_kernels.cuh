@@ -113,6 +113,15 @@ __device__ __forceinline__ uint64_t smem_desc(const void *p, uint32_t lbo, uint3
     return (uint64_t)((smem_u32(p) >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
            ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
 }
+// descriptor of a K-major tile in the 64-byte swizzled layout (rows of 32
+// BF16 = 64 bytes, 8-row atoms of 512 bytes, 16-byte chunks exchanged by
+// the TMA's 64-byte swizzle): stride byte offset 512 between 8-row groups,
+// leading byte offset unused (16), layout type 4 (64-byte swizzle); a K step
+// of 16 elements inside the row advances the start address by 32 bytes
+__device__ __forceinline__ uint64_t smem_desc_sw64(const void *p) {
+    return (uint64_t)((smem_u32(p) >> 4) & 0x3FFFu) | ((uint64_t)(16 >> 4) << 16) | ((uint64_t)(512 >> 4) << 32) |
+           (1ull << 46) | (4ull << 61);
+}
 // instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both
 // K-major, N >> 3 and M >> 4
 __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
@@ -328,26 +337,27 @@ __device__ __forceinline__ void load_2d(void *dst, const CUtensorMap *m, int c0,
 }  // namespace tma
 
 constexpr int kConvTmaStages = 4;
-// barriers + tensor-memory address (128 bytes), then the stages: A (128
-// pixels x 32 channels) and B (BN output channels x 32 channels)
-__host__ __device__ constexpr int conv_tma_smem_bytes(int bn) { return 128 + kConvTmaStages * (kBM + bn) * kBK * 2; }
+// barriers + tensor-memory address in the first 1 KB, then the stages (1 KB
+// aligned for the swizzle): A (128 pixels x 32 channels) and B (BN output
+// channels x 32 channels), 64 bytes per row
+__host__ __device__ constexpr int conv_tma_smem_bytes(int bn) { return 1024 + kConvTmaStages * (kBM + bn) * kBK * 2; }
 
 // The convolution with its operand tiles brought in by TMA, for images whose
 // 128-pixel blocks are whole rows or row segments (width a multiple of 128,
 // or 128 / width rows with the height a multiple of that).  The activations
 // are a rank-4 tensor map (channel, column, row, image) over the input
-// slice: the tile of tap (dy, dx) is the box of 8 channels x bw columns x bh
-// rows at (ci, x0 + dx, y0 + dy, image), and the map's zero fill outside the
-// image is the convolution's zero padding.  Each box lands as 128 pixels x 16
-// bytes, the K-major core-matrix layout with 8-pixel groups 128 bytes apart
-// (stride byte offset) and 8-channel groups 2048 bytes apart (leading byte
-// offset); the weights [cout][9 cin] are a rank-2 map read the same way.  One
-// thread runs the whole loop: it keeps all four stages in flight, waits for a
-// stage's bytes on its `full` mbarrier, issues the two MMAs, commits them to
-// the stage's `empty` mbarrier and refills the stage used one step earlier
-// once those MMAs are done.  The other threads wait for the epilogue.  Waits
-// are bounded; after one runs out the block lets its transfers land and its
-// MMAs finish (bounded), flags err, releases the tensor memory and returns.
+// slice: the tile of tap (dy, dx) is the box of 32 channels x bw columns x
+// bh rows at (ci, x0 + dx, y0 + dy, image), and the map's zero fill outside
+// the image is the convolution's zero padding.  Each box lands as 128 rows
+// (pixels) of 64 bytes in the 64-byte swizzled K-major layout, which the MMA
+// descriptors read directly; the weights [cout][9 cin] are a rank-2 map read
+// the same way.  One thread runs the whole loop: it keeps all four stages in
+// flight, waits for a stage's bytes on its `full` mbarrier, issues the two
+// MMAs, commits them to the stage's `empty` mbarrier and refills the stage
+// used one step earlier once those MMAs are done.  The other threads wait
+// for the epilogue.  Waits are bounded; after one runs out the block lets its
+// transfers land and its MMAs finish (bounded), flags err, releases the
+// tensor memory and returns.
 template <int BN>
 __global__ void __launch_bounds__(128) conv3x3_tma_kernel(const __grid_constant__ CUtensorMap tmA,
                                                           const __grid_constant__ CUtensorMap tmB, ConvArgs a,
@@ -358,8 +368,14 @@ __global__ void __launch_bounds__(128) conv3x3_tma_kernel(const __grid_constant_
     uint64_t *full = reinterpret_cast<uint64_t *>(sm);
     uint64_t *empty = full + NS;
     uint32_t *s_taddr = reinterpret_cast<uint32_t *>(empty + NS);
-    unsigned char *stages = sm + 128;
+    unsigned char *stages = sm + 1024;
     const int tid = threadIdx.x, warp = tid >> 5;
+    // the swizzled tiles need 1 KB aligned buffers: if the runtime ever placed
+    // the dynamic shared memory otherwise, flag and stop before any transfer
+    if (smem_u32(stages) & 1023u) {
+        if (tid == 0) atomicOr(err, 2);
+        return;
+    }
     const long P = (long)a.n * a.h * a.wd;
     const long p0 = (long)blockIdx.x * kBM;
     const int co0 = blockIdx.y * BN;
@@ -388,10 +404,8 @@ __global__ void __launch_bounds__(128) conv3x3_tma_kernel(const __grid_constant_
             uint64_t *fb = &full[s % NS];
             const int dy = tap_i / 3 - 1, dx = tap_i % 3 - 1, ci0 = cs_i * kBK;
             tma::arrive_expect_tx(fb, (uint32_t)S_BYTES);
-#pragma unroll
-            for (int g = 0; g < kBK / 8; ++g) tma::load_4d(A + g * (kBM * 16), &tmA, ci0 + 8 * g, x0 + dx, y0 + dy, img, fb);
-#pragma unroll
-            for (int g = 0; g < kBK / 8; ++g) tma::load_2d(B + g * (BN * 16), &tmB, tap_i * a.cin + ci0 + 8 * g, co0, fb);
+            tma::load_4d(A, &tmA, ci0, x0 + dx, y0 + dy, img, fb);
+            tma::load_2d(B, &tmB, tap_i * a.cin + ci0, co0, fb);
             if (++cs_i == csteps) {
                 cs_i = 0;
                 ++tap_i;
@@ -407,10 +421,9 @@ __global__ void __launch_bounds__(128) conv3x3_tma_kernel(const __grid_constant_
             tc::fence_after_sync();
             const unsigned char *A = stages + buf * S_BYTES, *B = A + A_BYTES;
 #pragma unroll
-            for (int kh = 0; kh < kBK / 16; ++kh)  // 16 channels (two 8-channel groups) per MMA
-                tc::mma_bf16(taddr, tc::smem_desc(A + kh * 2 * (kBM * 16), kBM * 16, 128),
-                             tc::smem_desc(B + kh * 2 * (BN * 16), BN * 16, 128), tc::idesc_bf16(kBM, BN),
-                             (ks > 0 || kh > 0) ? 1u : 0u);
+            for (int kh = 0; kh < kBK / 16; ++kh)  // 16 channels (32 bytes of the row) per MMA
+                tc::mma_bf16(taddr, tc::smem_desc_sw64(A + kh * 32), tc::smem_desc_sw64(B + kh * 32),
+                             tc::idesc_bf16(kBM, BN), (ks > 0 || kh > 0) ? 1u : 0u);
             tc::mma_commit(&empty[buf]);
             done = ks + 1;
             // refill the stage of step ks - 1: its MMAs precede this step's in
