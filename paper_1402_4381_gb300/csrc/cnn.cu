@@ -33,12 +33,36 @@ static const LayerSpec kLayers[14] = {
 enum { E0A, E0B, E1A, E1B, E2A, E2B, B3A, B3B, D2A, D2B, D1A, D1B, D0A, D0B, NL };
 
 // ---------------------------------------------------------------- elementwise kernels
+// One thread moves 8 channels (16 bytes) of one pixel; C / 8 = 2^lc8 chunks
+// per pixel (channel counts 32, 64, 128, 256), pixel indices below 2^31
+// (checked when the network is created).  Every output element is computed
+// with the same FP32 operations in the same order as an element-wise loop.
+__device__ __forceinline__ uint4 ld16(const __nv_bfloat16 *p) { return *reinterpret_cast<const uint4 *>(p); }
+__device__ __forceinline__ void st16(__nv_bfloat16 *p, const uint4 &v) { *reinterpret_cast<uint4 *>(p) = v; }
+__device__ __forceinline__ void unpack8(const uint4 &u, float *f) {
+    const __nv_bfloat162 *h = reinterpret_cast<const __nv_bfloat162 *>(&u);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float2 t = __bfloat1622float2(h[k]);
+        f[2 * k] = t.x;
+        f[2 * k + 1] = t.y;
+    }
+}
+__device__ __forceinline__ uint4 pack8(const float *f) {
+    uint4 u;
+    __nv_bfloat162 *h = reinterpret_cast<__nv_bfloat162 *>(&u);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) h[k] = __floats2bfloat162_rn(f[2 * k], f[2 * k + 1]);
+    return u;
+}
+
+// input image x * s in channel 0 of 32 (the others zero)
 __global__ void pack_input_kernel(const float *__restrict__ x, __nv_bfloat16 *__restrict__ out, long P, float s) {
-    const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= P * 32) return;
-    const long p = i >> 5;
-    const int c = (int)(i & 31);
-    out[i] = __float2bfloat16_rn(c == 0 ? x[p] * s : 0.f);
+    const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;  // chunk: pixel i / 4, channels 8 (i % 4)
+    if (i >= P * 4) return;
+    float f[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if ((i & 3) == 0) f[0] = x[i >> 2] * s;
+    st16(out + i * 8, pack8(f));
 }
 
 // y = x (scaled) + b + sum_c w[c] h[p][c]; optional loss against t (scaled):
@@ -84,13 +108,22 @@ __global__ void output_bwd_kernel(const float *__restrict__ dy, const __nv_bfloa
 #pragma unroll
     for (int c = 0; c < 32; ++c) part[c] = 0.f;
     float pb = 0.f;
+    float wr[32];
+#pragma unroll
+    for (int c = 0; c < 32; ++c) wr[c] = w[c];
     for (long p = (long)blockIdx.x * blockDim.x + tid; p < P; p += (long)gridDim.x * blockDim.x) {
         const float g = dy[p];
         pb += g;
 #pragma unroll
-        for (int c = 0; c < 32; ++c) {
-            dh[p * 32 + c] = __float2bfloat16_rn(g * w[c]);
-            part[c] = fmaf(g, __bfloat162float(h[p * 32 + c]), part[c]);
+        for (int q = 0; q < 4; ++q) {  // 8 channels (16 bytes) at a time
+            float hv[8], o[8];
+            unpack8(ld16(h + p * 32 + 8 * q), hv);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                o[k] = g * wr[8 * q + k];
+                part[8 * q + k] = fmaf(g, hv[k], part[8 * q + k]);
+            }
+            st16(dh + p * 32 + 8 * q, pack8(o));
         }
     }
 #pragma unroll
@@ -108,14 +141,20 @@ __global__ void output_bwd_kernel(const float *__restrict__ dy, const __nv_bfloa
 
 // dz[p][c] = y[p][c] > 0 ? dy[p][c] : 0 (compact output)
 __global__ void relu_bwd_kernel(const __nv_bfloat16 *__restrict__ y, int ld_y, int coff_y,
-                                const __nv_bfloat16 *__restrict__ dy, int ld_dy, int coff_dy, int C, long P,
+                                const __nv_bfloat16 *__restrict__ dy, int ld_dy, int coff_dy, int lc8, long P,
                                 __nv_bfloat16 *__restrict__ dz) {
     const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= P * C) return;
-    const long p = i / C;
-    const int c = (int)(i - p * C);
-    const float v = __bfloat162float(y[p * ld_y + coff_y + c]);
-    dz[i] = v > 0.f ? dy[p * ld_dy + coff_dy + c] : __float2bfloat16_rn(0.f);
+    if (i >= (P << lc8)) return;
+    const long p = i >> lc8;
+    const int c = (int)(i & ((1 << lc8) - 1)) * 8;
+    const uint4 yv = ld16(y + p * ld_y + coff_y + c), gv = ld16(dy + p * ld_dy + coff_dy + c);
+    const __nv_bfloat16 *ys = reinterpret_cast<const __nv_bfloat16 *>(&yv);
+    const __nv_bfloat16 *gs = reinterpret_cast<const __nv_bfloat16 *>(&gv);
+    uint4 o;
+    __nv_bfloat16 *os = reinterpret_cast<__nv_bfloat16 *>(&o);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) os[k] = __bfloat162float(ys[k]) > 0.f ? gs[k] : __float2bfloat16_rn(0.f);
+    st16(dz + i * 8, o);
 }
 
 // db[c] += sum_p dz[p][c]
@@ -130,79 +169,86 @@ __global__ void bias_grad_kernel(const __nv_bfloat16 *__restrict__ dz, int C, lo
 }
 
 // 2x2 average pooling of an NHWC slice
-__global__ void pool_kernel(const __nv_bfloat16 *__restrict__ in, int ld_in, int coff_in, int C, int n, int h, int w,
+__global__ void pool_kernel(const __nv_bfloat16 *__restrict__ in, int ld_in, int coff_in, int lc8, int n, int h, int w,
                             __nv_bfloat16 *__restrict__ out) {
     const int h2 = h / 2, w2 = w / 2;
-    const long total = (long)n * h2 * w2 * C;
+    const long total = ((long)n * h2 * w2) << lc8;
     const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= total) return;
-    const int c = (int)(i % C);
-    long q = i / C;
-    const int x = (int)(q % w2);
-    q /= w2;
-    const int y = (int)(q % h2);
-    const long img = q / h2;
-    const long p00 = (img * h + 2 * y) * w + 2 * x;
-    float s = 0.f;
-    s += __bfloat162float(in[p00 * ld_in + coff_in + c]);
-    s += __bfloat162float(in[(p00 + 1) * ld_in + coff_in + c]);
-    s += __bfloat162float(in[(p00 + w) * ld_in + coff_in + c]);
-    s += __bfloat162float(in[(p00 + w + 1) * ld_in + coff_in + c]);
-    out[i] = __float2bfloat16_rn(0.25f * s);
+    const int c = (int)(i & ((1 << lc8) - 1)) * 8;
+    const unsigned q = (unsigned)(i >> lc8);
+    const unsigned x = q % w2, t = q / w2, y = t % h2, img = t / h2;
+    const long p00 = ((long)img * h + 2 * y) * w + 2 * x;
+    const long src[4] = {p00, p00 + 1, p00 + w, p00 + w + 1};
+    float s[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, v[8];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        unpack8(ld16(in + src[j] * ld_in + coff_in + c), v);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) s[k] += v[k];
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s[k] = 0.25f * s[k];
+    st16(out + i * 8, pack8(s));
 }
 
 // gradient of pooling plus a skip gradient slice: out[p][c] = dpool[p/2][c] / 4 + add[p][c]
 __global__ void pool_bwd_kernel(const __nv_bfloat16 *__restrict__ dpool, const __nv_bfloat16 *__restrict__ add,
-                                int ld_add, int coff_add, int C, int n, int h, int w, __nv_bfloat16 *__restrict__ out) {
-    const long total = (long)n * h * w * C;
+                                int ld_add, int coff_add, int lc8, int n, int h, int w, __nv_bfloat16 *__restrict__ out) {
+    const long total = ((long)n * h * w) << lc8;
     const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= total) return;
-    const int c = (int)(i % C);
-    const long p = i / C;
-    const int x = (int)(p % w);
-    const long q = p / w;
-    const int y = (int)(q % h);
-    const long img = q / h;
-    const long pp = (img * (h / 2) + y / 2) * (w / 2) + x / 2;
-    const float v = 0.25f * __bfloat162float(dpool[pp * C + c]) + __bfloat162float(add[p * ld_add + coff_add + c]);
-    out[i] = __float2bfloat16_rn(v);
+    const int c = (int)(i & ((1 << lc8) - 1)) * 8;
+    const unsigned p = (unsigned)(i >> lc8);
+    const unsigned x = p % w, q = p / w, y = q % h, img = q / h;
+    const long pp = ((long)img * (h / 2) + y / 2) * (w / 2) + x / 2;
+    float d[8], a[8];
+    unpack8(ld16(dpool + (pp << (lc8 + 3)) + c), d);
+    unpack8(ld16(add + (long)p * ld_add + coff_add + c), a);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) d[k] = 0.25f * d[k] + a[k];
+    st16(out + i * 8, pack8(d));
 }
 
 // nearest 2x upsampling of [n][h][w][C] into a slice of a [n][2h][2w][ld] buffer
-__global__ void up_kernel(const __nv_bfloat16 *__restrict__ in, int C, int n, int h, int w,
+// (one thread per low-resolution chunk, written to its 2x2 block)
+__global__ void up_kernel(const __nv_bfloat16 *__restrict__ in, int lc8, int n, int h, int w,
                           __nv_bfloat16 *__restrict__ out, int ld_out, int coff_out) {
-    const long total = (long)n * 4 * h * w * C;
+    const long total = ((long)n * h * w) << lc8;
     const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= total) return;
-    const int c = (int)(i % C);
-    const long p = i / C;
-    const int x = (int)(p % (2 * w));
-    const long q = p / (2 * w);
-    const int y = (int)(q % (2 * h));
-    const long img = q / (2 * h);
-    out[p * ld_out + coff_out + c] = in[((img * h + y / 2) * w + x / 2) * C + c];
+    const int c = (int)(i & ((1 << lc8) - 1)) * 8;
+    const unsigned q = (unsigned)(i >> lc8);
+    const unsigned x = q % w, t = q / w, y = t % h, img = t / h;
+    const uint4 v = ld16(in + i * 8);
+    const long W2 = 2L * w;
+    const long p00 = ((long)img * 2 * h + 2 * y) * W2 + 2 * x;
+    st16(out + p00 * ld_out + coff_out + c, v);
+    st16(out + (p00 + 1) * ld_out + coff_out + c, v);
+    st16(out + (p00 + W2) * ld_out + coff_out + c, v);
+    st16(out + (p00 + W2 + 1) * ld_out + coff_out + c, v);
 }
 
 // gradient of upsampling: out[p][c] = sum of the 2x2 block of a gradient slice
-__global__ void up_bwd_kernel(const __nv_bfloat16 *__restrict__ g, int ld_g, int coff_g, int C, int n, int h, int w,
+__global__ void up_bwd_kernel(const __nv_bfloat16 *__restrict__ g, int ld_g, int coff_g, int lc8, int n, int h, int w,
                               __nv_bfloat16 *__restrict__ out) {
-    const long total = (long)n * h * w * C;  // h, w: the low-resolution size
+    const long total = ((long)n * h * w) << lc8;  // h, w: the low-resolution size
     const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= total) return;
-    const int c = (int)(i % C);
-    const long p = i / C;
-    const int x = (int)(p % w);
-    const long q = p / w;
-    const int y = (int)(q % h);
-    const long img = q / h;
-    const int W2 = 2 * w;
-    const long p00 = (img * 2 * h + 2 * y) * W2 + 2 * x;
-    float s = 0.f;
-    s += __bfloat162float(g[p00 * ld_g + coff_g + c]);
-    s += __bfloat162float(g[(p00 + 1) * ld_g + coff_g + c]);
-    s += __bfloat162float(g[(p00 + W2) * ld_g + coff_g + c]);
-    s += __bfloat162float(g[(p00 + W2 + 1) * ld_g + coff_g + c]);
-    out[i] = __float2bfloat16_rn(s);
+    const int c = (int)(i & ((1 << lc8) - 1)) * 8;
+    const unsigned q = (unsigned)(i >> lc8);
+    const unsigned x = q % w, t = q / w, y = t % h, img = t / h;
+    const long W2 = 2L * w;
+    const long p00 = ((long)img * 2 * h + 2 * y) * W2 + 2 * x;
+    const long src[4] = {p00, p00 + 1, p00 + W2, p00 + W2 + 1};
+    float s[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, v[8];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        unpack8(ld16(g + src[j] * ld_g + coff_g + c), v);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) s[k] += v[k];
+    }
+    st16(out + i * 8, pack8(s));
 }
 
 // BF16 working copies of one layer: w [co][tap][ci] and the transposed,
@@ -233,6 +279,12 @@ __global__ void adam_kernel(float *__restrict__ w, const float *__restrict__ g, 
 }
 
 static inline unsigned nb(long n, int t) { return (unsigned)((n + t - 1) / t); }
+// log2 of C / 8 for the 16-byte elementwise kernels (C = 32, 64, 128 or 256)
+static inline int lc8(int C) {
+    int l = 0;
+    while ((8 << l) < C) ++l;
+    return l;
+}
 
 }  // namespace cnn
 }  // namespace oslalm
@@ -378,6 +430,47 @@ int conv(const oslalm_cnn *c, const __nv_bfloat16 *in, int ld_in, int coff_in, i
     return OSLALM_OK;
 }
 
+// Tensor maps of the TMA weight gradient: dz [P][cout] (slice of ld_dz
+// channels at coff_dz) as (channel, pixel) with boxes of 32 x 64, the x slice
+// as (channel, column, row, image) with boxes of 32 channels x bw x bh (64
+// pixels), both in the 64-byte swizzle.  False if the geometry or the
+// alignment does not allow it.
+bool wgrad_tensor_maps(const __nv_bfloat16 *dz, int ld_dz, int coff_dz, int cout, const __nv_bfloat16 *x, int ld_x,
+                       int coff_x, int cin, int n, int h, int wd, CUtensorMap *ta, CUtensorMap *tb) {
+    int bw = 0, bh = 0;  // a 64-pixel stage: a row segment, or 64 / wd whole rows
+    if (wd % kWgBK == 0) {
+        bw = kWgBK;
+        bh = 1;
+    } else if (kWgBK % wd == 0 && h % (kWgBK / wd) == 0) {
+        bw = wd;
+        bh = kWgBK / wd;
+    } else {
+        return false;
+    }
+    const __nv_bfloat16 *a0 = dz + coff_dz, *b0 = x + coff_x;
+    if (reinterpret_cast<uintptr_t>(a0) % 16 || reinterpret_cast<uintptr_t>(b0) % 16 || ld_dz % 8 || ld_x % 8 ||
+        cin % 32 || cout % 32)
+        return false;
+    PFN_cuTensorMapEncodeTiled_v12000 enc = encode_tiled();
+    if (!enc) return false;
+    const cuuint64_t es = 2;
+    const long P = (long)n * h * wd;
+    const cuuint64_t gdA[2] = {(cuuint64_t)cout, (cuuint64_t)P};
+    const cuuint64_t gsA[1] = {(cuuint64_t)ld_dz * es};
+    const cuuint32_t boxA[2] = {32, (cuuint32_t)kWgBK};
+    const cuuint32_t one[4] = {1, 1, 1, 1};
+    if (enc(ta, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16 *>(a0), gdA, gsA, boxA, one,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return false;
+    const cuuint64_t gdB[4] = {(cuuint64_t)cin, (cuuint64_t)wd, (cuuint64_t)h, (cuuint64_t)n};
+    const cuuint64_t gsB[3] = {ld_x * es, (cuuint64_t)wd * ld_x * es, (cuuint64_t)h * wd * ld_x * es};
+    const cuuint32_t boxB[4] = {32, (cuuint32_t)bw, (cuuint32_t)bh, 1};
+    return enc(tb, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<__nv_bfloat16 *>(b0), gdB, gsB, boxB, one,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 int wgrad(const oslalm_cnn *c, const __nv_bfloat16 *dz, int cout, const __nv_bfloat16 *x, int ld_x, int coff_x,
           int cin, float *dw, int n, int h, int wd, cudaStream_t st) {
     WgradArgs a;
@@ -389,30 +482,63 @@ int wgrad(const oslalm_cnn *c, const __nv_bfloat16 *dz, int cout, const __nv_bfl
     int bn = 256;
     while (cin % bn) bn >>= 1;
     if (bn < 32 || cout % 8) return fail(OSLALM_ERR_ARG, "weight gradient needs channel counts that are multiples of 32");
+    int dev = 0, sms = 0, smem_sm = 0;
+    OSL_CUDA_TRY(cudaGetDevice(&dev));
+    OSL_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    OSL_CUDA_TRY(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+    // one wave of blocks (blocks per SM from shared memory and tensor-memory
+    // columns), the pixels split evenly in multiples of the 64-pixel stage
+    auto split = [&](int smem, long tiles) {
+        int occ = std::min(smem_sm / (smem + 1024), std::min(512 / bn, 16));
+        if (occ < 1) occ = 1;
+        long splits = ((long)sms * occ) / tiles;
+        if (splits < 1) splits = 1;
+        long per = (P + splits - 1) / splits;
+        per = ((per + kWgBK - 1) / kWgBK) * kWgBK;
+        a.pix_per_block = (int)per;
+        return dim3((cout + 127) / 128, 9 * (cin / bn), (unsigned)((P + per - 1) / per));
+    };
+    CUtensorMap ta, tb;
+    const int ga32 = std::min(4, cout / 32);
+    if (c->use_tma && cout % 32 == 0 && ga32 != 3 &&
+        wgrad_tensor_maps(dz, cout, 0, cout, x, ld_x, coff_x, cin, n, h, wd, &ta, &tb)) {
+        const int smem = wgrad_tma_smem_bytes(bn, ga32);
+        const dim3 grid = split(smem, (long)((cout + 127) / 128) * 9 * (cin / bn));
+#define OSL_WGT(BN, GA)                                                                                      \
+    do {                                                                                                     \
+        static bool opted = false;                                                                           \
+        if (!opted) {                                                                                        \
+            OSL_CUDA_TRY(cudaFuncSetAttribute(wgrad3x3_tma_kernel<BN, GA>,                                   \
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize,                   \
+                                              wgrad_tma_smem_bytes(BN, GA)));                                \
+            opted = true;                                                                                    \
+        }                                                                                                    \
+        wgrad3x3_tma_kernel<BN, GA><<<grid, 128, wgrad_tma_smem_bytes(BN, GA), st>>>(ta, tb, a, c->err);    \
+    } while (0)
+        switch (bn * 10 + ga32) {
+            case 321: OSL_WGT(32, 1); break;
+            case 322: OSL_WGT(32, 2); break;
+            case 324: OSL_WGT(32, 4); break;
+            case 641: OSL_WGT(64, 1); break;
+            case 642: OSL_WGT(64, 2); break;
+            case 644: OSL_WGT(64, 4); break;
+            case 1281: OSL_WGT(128, 1); break;
+            case 1282: OSL_WGT(128, 2); break;
+            case 1284: OSL_WGT(128, 4); break;
+            case 2561: OSL_WGT(256, 1); break;
+            case 2562: OSL_WGT(256, 2); break;
+            default: OSL_WGT(256, 4); break;
+        }
+#undef OSL_WGT
+        OSL_LAUNCH_CHECK("wgrad3x3_tma_kernel");
+        return OSLALM_OK;
+    }
     // dz channel groups staged per block: 4, 8 or 16 (output channel counts
     // of 32, 64 or a multiple of 128 ... any multiple of 8 from 128 on)
     const int ga = wgrad_groups(cout);
     if (ga != 4 && ga != 8 && ga != 16)
         return fail(OSLALM_ERR_ARG, "weight gradient needs 32, 64 or at least 128 output channels");
-    const int smem = wgrad_tc_smem_bytes(bn, ga);
-    const long tiles = (long)((cout + 127) / 128) * 9 * (cin / bn);
-    // blocks per SM: shared memory (1 KB reserved per block), tensor-memory
-    // columns (512 per SM), 16 blocks of 128 threads
-    int dev = 0, sms = 0, smem_sm = 0;
-    OSL_CUDA_TRY(cudaGetDevice(&dev));
-    OSL_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    OSL_CUDA_TRY(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
-    int occ = smem_sm / (smem + 1024);
-    occ = std::min(occ, std::min(512 / bn, 16));
-    if (occ < 1) occ = 1;
-    // one wave of blocks, the pixels split evenly (multiples of the 64-pixel
-    // stage) over the splits
-    long splits = ((long)sms * occ) / tiles;
-    if (splits < 1) splits = 1;
-    long per = (P + splits - 1) / splits;
-    per = ((per + kWgBK - 1) / kWgBK) * kWgBK;
-    a.pix_per_block = (int)per;
-    const dim3 grid((cout + 127) / 128, 9 * (cin / bn), (unsigned)((P + per - 1) / per));
+    const dim3 grid = split(wgrad_tc_smem_bytes(bn, ga), (long)((cout + 127) / 128) * 9 * (cin / bn));
 #define OSL_WG(BN, GA)                                                                                       \
     do {                                                                                                     \
         static bool opted = false; /* dynamic shared memory above 48 KB, once */                            \
@@ -452,7 +578,7 @@ int layer_bwd(oslalm_cnn *c, int L, int lvl, const __nv_bfloat16 *x, int ld_x, i
     const LayerSpec &s = kLayers[L];
     const int h = c->H >> lvl, w = c->W >> lvl;
     const long P = c->P[lvl];
-    relu_bwd_kernel<<<nb(P * s.cout, 256), 256, 0, st>>>(y, ld_y, coff_y, gy, ld_gy, coff_gy, s.cout, P, c->dz);
+    relu_bwd_kernel<<<nb(P * s.cout / 8, 256), 256, 0, st>>>(y, ld_y, coff_y, gy, ld_gy, coff_gy, lc8(s.cout), P, c->dz);
     OSL_LAUNCH_CHECK("relu_bwd_kernel");
     if (int rc = wgrad(c, c->dz, s.cout, x, ld_x, coff_x, s.cin, c->grad + c->off_w[L], c->batch, h, w, st)) return rc;
     bias_grad_kernel<<<std::min<long>(nb(P, 8), 2048), 256, 0, st>>>(c->dz, s.cout, P, c->grad + c->off_b[L]);
@@ -472,22 +598,22 @@ int forward_net(oslalm_cnn *c, cudaStream_t st) {
         return rc;
     C3(c->in0, 32, 0, 32, E0A, c->e0a, 32, 0, 32, 0);
     C3(c->e0a, 32, 0, 32, E0B, c->cat0, 96, 64, 32, 0);
-    pool_kernel<<<nb(c->P[1] * 32, 256), 256, 0, st>>>(c->cat0, 96, 64, 32, n, H, W, c->p0);
+    pool_kernel<<<nb(c->P[1] * 32 / 8, 256), 256, 0, st>>>(c->cat0, 96, 64, lc8(32), n, H, W, c->p0);
     C3(c->p0, 32, 0, 32, E1A, c->e1a, 64, 0, 64, 1);
     C3(c->e1a, 64, 0, 64, E1B, c->cat1, 192, 128, 64, 1);
-    pool_kernel<<<nb(c->P[2] * 64, 256), 256, 0, st>>>(c->cat1, 192, 128, 64, n, H / 2, W / 2, c->p1);
+    pool_kernel<<<nb(c->P[2] * 64 / 8, 256), 256, 0, st>>>(c->cat1, 192, 128, lc8(64), n, H / 2, W / 2, c->p1);
     C3(c->p1, 64, 0, 64, E2A, c->e2a, 128, 0, 128, 2);
     C3(c->e2a, 128, 0, 128, E2B, c->cat2, 384, 256, 128, 2);
-    pool_kernel<<<nb(c->P[3] * 128, 256), 256, 0, st>>>(c->cat2, 384, 256, 128, n, H / 4, W / 4, c->p2);
+    pool_kernel<<<nb(c->P[3] * 128 / 8, 256), 256, 0, st>>>(c->cat2, 384, 256, lc8(128), n, H / 4, W / 4, c->p2);
     C3(c->p2, 128, 0, 128, B3A, c->b3a, 256, 0, 256, 3);
     C3(c->b3a, 256, 0, 256, B3B, c->b3b, 256, 0, 256, 3);
-    up_kernel<<<nb(c->P[2] * 256, 256), 256, 0, st>>>(c->b3b, 256, n, H / 8, W / 8, c->cat2, 384, 0);
+    up_kernel<<<nb(c->P[3] * 256 / 8, 256), 256, 0, st>>>(c->b3b, lc8(256), n, H / 8, W / 8, c->cat2, 384, 0);
     C3(c->cat2, 384, 0, 384, D2A, c->d2a, 128, 0, 128, 2);
     C3(c->d2a, 128, 0, 128, D2B, c->d2b, 128, 0, 128, 2);
-    up_kernel<<<nb(c->P[1] * 128, 256), 256, 0, st>>>(c->d2b, 128, n, H / 4, W / 4, c->cat1, 192, 0);
+    up_kernel<<<nb(c->P[2] * 128 / 8, 256), 256, 0, st>>>(c->d2b, lc8(128), n, H / 4, W / 4, c->cat1, 192, 0);
     C3(c->cat1, 192, 0, 192, D1A, c->d1a, 64, 0, 64, 1);
     C3(c->d1a, 64, 0, 64, D1B, c->d1b, 64, 0, 64, 1);
-    up_kernel<<<nb(c->P[0] * 64, 256), 256, 0, st>>>(c->d1b, 64, n, H / 2, W / 2, c->cat0, 96, 0);
+    up_kernel<<<nb(c->P[1] * 64 / 8, 256), 256, 0, st>>>(c->d1b, lc8(64), n, H / 2, W / 2, c->cat0, 96, 0);
     C3(c->cat0, 96, 0, 96, D0A, c->d0a, 32, 0, 32, 0);
     C3(c->d0a, 32, 0, 32, D0B, c->d0b, 32, 0, 32, 0);
 #undef C3
@@ -506,23 +632,23 @@ int backward_net(oslalm_cnn *c, cudaStream_t st) {
     // decoder level 0: ga = d(d0b) -> gb = d(d0a) -> g_cat0
     if ((rc = layer_bwd(c, D0B, 0, c->d0a, 32, 0, c->d0b, 32, 0, c->ga, 32, 0, c->gb, 32, 0, st))) return rc;
     if ((rc = layer_bwd(c, D0A, 0, c->cat0, 96, 0, c->d0a, 32, 0, c->gb, 32, 0, c->g_cat0, 96, 0, st))) return rc;
-    up_bwd_kernel<<<nb(c->P[1] * 64, 256), 256, 0, st>>>(c->g_cat0, 96, 0, 64, n, H / 2, W / 2, c->ga);  // d(d1b)
+    up_bwd_kernel<<<nb(c->P[1] * 64 / 8, 256), 256, 0, st>>>(c->g_cat0, 96, 0, lc8(64), n, H / 2, W / 2, c->ga);  // d(d1b)
     if ((rc = layer_bwd(c, D1B, 1, c->d1a, 64, 0, c->d1b, 64, 0, c->ga, 64, 0, c->gb, 64, 0, st))) return rc;
     if ((rc = layer_bwd(c, D1A, 1, c->cat1, 192, 0, c->d1a, 64, 0, c->gb, 64, 0, c->g_cat1, 192, 0, st))) return rc;
-    up_bwd_kernel<<<nb(c->P[2] * 128, 256), 256, 0, st>>>(c->g_cat1, 192, 0, 128, n, H / 4, W / 4, c->ga);  // d(d2b)
+    up_bwd_kernel<<<nb(c->P[2] * 128 / 8, 256), 256, 0, st>>>(c->g_cat1, 192, 0, lc8(128), n, H / 4, W / 4, c->ga);  // d(d2b)
     if ((rc = layer_bwd(c, D2B, 2, c->d2a, 128, 0, c->d2b, 128, 0, c->ga, 128, 0, c->gb, 128, 0, st))) return rc;
     if ((rc = layer_bwd(c, D2A, 2, c->cat2, 384, 0, c->d2a, 128, 0, c->gb, 128, 0, c->g_cat2, 384, 0, st))) return rc;
-    up_bwd_kernel<<<nb(c->P[3] * 256, 256), 256, 0, st>>>(c->g_cat2, 384, 0, 256, n, H / 8, W / 8, c->ga);  // d(b3b)
+    up_bwd_kernel<<<nb(c->P[3] * 256 / 8, 256), 256, 0, st>>>(c->g_cat2, 384, 0, lc8(256), n, H / 8, W / 8, c->ga);  // d(b3b)
     if ((rc = layer_bwd(c, B3B, 3, c->b3a, 256, 0, c->b3b, 256, 0, c->ga, 256, 0, c->gb, 256, 0, st))) return rc;
     if ((rc = layer_bwd(c, B3A, 3, c->p2, 128, 0, c->b3a, 256, 0, c->gb, 256, 0, c->ga, 128, 0, st))) return rc;
     // pool 2 backward + skip gradient -> d(e2b) in gb
-    pool_bwd_kernel<<<nb(c->P[2] * 128, 256), 256, 0, st>>>(c->ga, c->g_cat2, 384, 256, 128, n, H / 4, W / 4, c->gb);
+    pool_bwd_kernel<<<nb(c->P[2] * 128 / 8, 256), 256, 0, st>>>(c->ga, c->g_cat2, 384, 256, lc8(128), n, H / 4, W / 4, c->gb);
     if ((rc = layer_bwd(c, E2B, 2, c->e2a, 128, 0, c->cat2, 384, 256, c->gb, 128, 0, c->ga, 128, 0, st))) return rc;
     if ((rc = layer_bwd(c, E2A, 2, c->p1, 64, 0, c->e2a, 128, 0, c->ga, 128, 0, c->gb, 64, 0, st))) return rc;
-    pool_bwd_kernel<<<nb(c->P[1] * 64, 256), 256, 0, st>>>(c->gb, c->g_cat1, 192, 128, 64, n, H / 2, W / 2, c->ga);
+    pool_bwd_kernel<<<nb(c->P[1] * 64 / 8, 256), 256, 0, st>>>(c->gb, c->g_cat1, 192, 128, lc8(64), n, H / 2, W / 2, c->ga);
     if ((rc = layer_bwd(c, E1B, 1, c->e1a, 64, 0, c->cat1, 192, 128, c->ga, 64, 0, c->gb, 64, 0, st))) return rc;
     if ((rc = layer_bwd(c, E1A, 1, c->p0, 32, 0, c->e1a, 64, 0, c->gb, 64, 0, c->ga, 32, 0, st))) return rc;
-    pool_bwd_kernel<<<nb(c->P[0] * 32, 256), 256, 0, st>>>(c->ga, c->g_cat0, 96, 64, 32, n, H, W, c->gb);
+    pool_bwd_kernel<<<nb(c->P[0] * 32 / 8, 256), 256, 0, st>>>(c->ga, c->g_cat0, 96, 64, lc8(32), n, H, W, c->gb);
     if ((rc = layer_bwd(c, E0B, 0, c->e0a, 32, 0, c->cat0, 96, 64, c->gb, 32, 0, c->ga, 32, 0, st))) return rc;
     if ((rc = layer_bwd(c, E0A, 0, c->in0, 32, 0, c->e0a, 32, 0, c->ga, 32, 0, nullptr, 0, 0, st))) return rc;
     OSL_LAUNCH_CHECK("backward");
@@ -558,7 +684,7 @@ int check_waits(oslalm_cnn *c) {
 
 int run_forward(oslalm_cnn *c, const float *x, const float *t, float s, float *y, cudaStream_t st) {
     const long P0 = c->P[0];
-    pack_input_kernel<<<nb(P0 * 32, 256), 256, 0, st>>>(x, c->in0, P0, s);
+    pack_input_kernel<<<nb(P0 * 4, 256), 256, 0, st>>>(x, c->in0, P0, s);
     OSL_LAUNCH_CHECK("pack_input_kernel");
     if (int rc = forward_net(c, st)) return rc;
     if (t) OSL_CUDA_TRY(cudaMemsetAsync(c->loss, 0, sizeof(double), st));
@@ -614,6 +740,7 @@ int oslalm_cnn_create(int batch, int height, int width, unsigned long long seed,
     *out = nullptr;
     if (batch <= 0 || height <= 0 || width <= 0 || height % 8 || width % 8)
         return fail(OSLALM_ERR_ARG, "need batch > 0 and height, width positive multiples of 8");
+    if ((long)batch * height * width >= (1L << 31)) return fail(OSLALM_ERR_ARG, "need batch x height x width < 2^31");
     oslalm_cnn *c = new (std::nothrow) oslalm_cnn();
     if (!c) return fail(OSLALM_ERR_ALLOC, "host allocation failed");
     c->batch = batch;

@@ -666,5 +666,144 @@ __global__ void __launch_bounds__(128) wgrad3x3_tc_kernel(WgradArgs a, int *err)
     if (warp == 0) tc::tmem_dealloc(taddr, BN);
 }
 
+// ---------------------------------------------------------------- weight gradient by TMA
+// descriptor of an MN-major tile in the 64-byte swizzled layout: rows are K
+// (pixels) of 64 bytes = 32 channels of MN, 8-row groups 512 bytes apart
+// (stride byte offset), 32-channel atoms `lbo` bytes apart (leading byte
+// offset), layout type 4 (64-byte swizzle)
+__device__ __forceinline__ uint64_t smem_desc_mn_sw64(const void *p, uint32_t lbo) {
+    return (uint64_t)((smem_u32(p) >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)(512 >> 4) << 32) | (1ull << 46) | (4ull << 61);
+}
+
+constexpr int kWgTmaStages = 4;
+constexpr int kWgTmaAtom = kWgBK * 64;  // one 32-channel atom of a stage: 64 pixels x 64 bytes
+// barriers (1 KB), the stages (ga32 atoms of dz, bn / 32 atoms of x each),
+// then a pad of 4 atoms that the unstaged A rows of the last stage may reach
+__host__ __device__ constexpr int wgrad_tma_smem_bytes(int bn, int ga32) {
+    return 1024 + kWgTmaStages * (ga32 + bn / 32) * kWgTmaAtom + 4 * kWgTmaAtom;
+}
+
+// The weight gradient with both operands brought in by TMA, for images whose
+// 64-pixel stages are row segments or whole rows (width a multiple of 64, or
+// 64 / width rows with the height a multiple of that): dz as a rank-2 map
+// (channel, pixel) with boxes of 32 channels x 64 pixels, x as a rank-4 map
+// (channel, column, row, image) with boxes of 32 channels x bw x bh at the
+// tap's shift, whose zero fill outside the image drops the pixels the tap
+// does not reach.  Each box is 64 rows (pixels, K) of 64 bytes (32 channels,
+// MN) in the 64-byte swizzle, which the MMA reads as an MN-major operand.
+// GA32 = min(4, cout / 32) atoms of dz are staged; as in wgrad3x3_tc_kernel
+// the other A rows read past the stage and only make accumulator rows that
+// are never stored.  One thread runs the loop over the block's stages (four
+// in flight, full / empty mbarriers, bounded waits), as in
+// conv3x3_tma_kernel; the epilogue adds the accumulator to dw with atomics.
+template <int BN, int GA32>
+__global__ void __launch_bounds__(128) wgrad3x3_tma_kernel(const __grid_constant__ CUtensorMap tmA,
+                                                           const __grid_constant__ CUtensorMap tmB, WgradArgs a,
+                                                           int *err) {
+    extern __shared__ __align__(1024) unsigned char sm[];
+    constexpr int NS = kWgTmaStages, BM = 128, BK = kWgBK;
+    constexpr int A_BYTES = GA32 * kWgTmaAtom, B_BYTES = (BN / 32) * kWgTmaAtom, S_BYTES = A_BYTES + B_BYTES;
+    uint64_t *full = reinterpret_cast<uint64_t *>(sm);
+    uint64_t *empty = full + NS;
+    uint32_t *s_taddr = reinterpret_cast<uint32_t *>(empty + NS);
+    unsigned char *stages = sm + 1024;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (smem_u32(stages) & 1023u) {  // the swizzle needs 1 KB aligned buffers
+        if (tid == 0) atomicOr(err, 2);
+        return;
+    }
+    const long P = (long)a.n * a.h * a.wd;
+    const int co0 = blockIdx.x * BM;
+    const int tap = blockIdx.y / (a.cin / BN);
+    const int ci0 = (blockIdx.y % (a.cin / BN)) * BN;
+    const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+    const long pbeg = (long)blockIdx.z * a.pix_per_block;
+    const long pend = pbeg + a.pix_per_block < P ? pbeg + a.pix_per_block : P;
+    const int nk = pend > pbeg ? (int)((pend - pbeg) / BK) : 0;  // whole stages (P, pix_per_block: multiples of 64)
+    if (warp == 0) tc::tmem_alloc(s_taddr, BN);
+    if (tid < 2 * NS) tc::mbar_init(&full[tid], 1);
+    tc::fence_barrier_init();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t taddr = *s_taddr;
+    bool ok = true;
+    if (tid == 0) {
+        tma::prefetch_map(&tmA);
+        tma::prefetch_map(&tmB);
+        const long hw = (long)a.h * a.wd;
+        int issued = 0, done = 0;
+        auto issue = [&]() {
+            const int s = issued++;
+            const long pb = pbeg + (long)s * BK;
+            const int img = (int)(pb / hw);
+            const int rem = (int)(pb - (long)img * hw);
+            const int y0 = rem / a.wd, x0 = rem - (rem / a.wd) * a.wd;
+            unsigned char *A = stages + (s % NS) * S_BYTES, *B = A + A_BYTES;
+            uint64_t *fb = &full[s % NS];
+            tma::arrive_expect_tx(fb, (uint32_t)S_BYTES);
+#pragma unroll
+            for (int g = 0; g < GA32; ++g) tma::load_2d(A + g * kWgTmaAtom, &tmA, co0 + 32 * g, (int)pb, fb);
+#pragma unroll
+            for (int g = 0; g < BN / 32; ++g)
+                tma::load_4d(B + g * kWgTmaAtom, &tmB, ci0 + 32 * g, x0 + dx, y0 + dy, img, fb);
+        };
+        while (issued < NS && issued < nk) issue();
+        constexpr uint32_t idesc = tc::idesc_bf16(BM, BN) | (1u << 15) | (1u << 16);  // A and B MN-major
+        for (int ks = 0; ks < nk; ++ks) {
+            const int buf = ks % NS;
+            if (!tc::mbar_wait(&full[buf], (ks / NS) & 1)) {
+                ok = false;
+                break;
+            }
+            tc::fence_after_sync();
+            const unsigned char *A = stages + buf * S_BYTES, *B = A + A_BYTES;
+#pragma unroll
+            for (int kh = 0; kh < BK / 16; ++kh)  // 16 pixels (two 8-row groups) per MMA
+                tc::mma_bf16(taddr, smem_desc_mn_sw64(A + kh * 1024, kWgTmaAtom),
+                             smem_desc_mn_sw64(B + kh * 1024, kWgTmaAtom), idesc, (ks > 0 || kh > 0) ? 1u : 0u);
+            tc::mma_commit(&empty[buf]);
+            done = ks + 1;
+            if (ks >= 1 && issued < nk) {
+                if (!tc::mbar_wait(&empty[(ks - 1) % NS], ((ks - 1) / NS) & 1)) {
+                    ok = false;
+                    break;
+                }
+                issue();
+            }
+        }
+        if (ok && nk > 0) ok = tc::mbar_wait(&empty[(nk - 1) % NS], ((nk - 1) / NS) & 1);
+        if (!ok) {
+            atomicOr(err, 1);
+            for (int s = done; s < issued; ++s) tc::mbar_wait(&full[s % NS], (s / NS) & 1);
+            if (done > 0) tc::mbar_wait(&empty[(done - 1) % NS], ((done - 1) / NS) & 1);
+        }
+    }
+    if (!__syncthreads_and(ok)) {
+        tc::fence_before_sync();
+        __syncthreads();
+        if (warp == 0) tc::tmem_dealloc(taddr, BN);
+        return;
+    }
+    tc::fence_after_sync();
+    if (nk > 0 && co0 + warp * 32 < a.cout) {
+        const int co = co0 + warp * 32 + lane;  // this thread's accumulator row (tensor-memory lane)
+#pragma unroll 1
+        for (int c = 0; c < BN; c += 8) {
+            float v[8];
+            tc::tmem_ld8(taddr + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, v);
+            if (co < a.cout) {
+                float *d = a.dw + ((long)co * 9 + tap) * a.cin + ci0 + c;
+#pragma unroll
+                for (int i = 0; i < 8; ++i) atomicAdd(d + i, v[i]);
+            }
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(taddr, BN);
+}
+
 }  // namespace cnn
 }  // namespace oslalm
