@@ -774,7 +774,7 @@ def run_cnn(args):
                                         "flop_per_image_forward": fpi,
                                         "l2": "activations of one step (~1 GB) exceed the L2"},
         "forward_only": {"value": tf_fwd, "unit": "TFLOP/s", "ms_per_batch": ms_fwd},
-        "roofline": {"kernel": "conv3x3_kernel + wgrad3x3_tc_kernel (tcgen05)", "bound": "tensor",
+        "roofline": {"kernel": "conv3x3_tma_kernel + wgrad3x3_tma_kernel (tcgen05, TMA)", "bound": "tensor",
                      "achieved": tf_train, "peak": peak, "unit": "TFLOP/s", "frac": tf_train / peak,
                      "traffic": None, "peak_basis": "measured cuBLAS BF16, sustained"},
         "gpu_launches": None, "clocks": clocks,
