@@ -170,7 +170,8 @@ def peaks():
 # one ncu capture, keyed by a hash of the 2D kernel sources it was taken on:
 # when the sources change, the figure no longer describes the kernel and the
 # bench reports traffic as null until a new capture is recorded here.
-NCU_DRAM_FAN = {"sources": None, "bytes": {}}
+NCU_DRAM_FAN = {"sources": "5eadf27ed026415c",
+                "bytes": {"bp2d_kernel": 3469824, "fp2d_kernel": 2443008, "update2d_kernel": 3679232}}
 KERNEL_SOURCES_2D = ("kernels2d.cu", "proj2d.cuh", "kernels_common.cuh", "common.cuh")
 
 
