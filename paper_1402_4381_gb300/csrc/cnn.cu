@@ -139,33 +139,44 @@ __global__ void output_bwd_kernel(const float *__restrict__ dy, const __nv_bfloa
     if (tid == 32) atomicAdd(db, sw[32]);
 }
 
-// dz[p][c] = y[p][c] > 0 ? dy[p][c] : 0 (compact output)
-__global__ void relu_bwd_kernel(const __nv_bfloat16 *__restrict__ y, int ld_y, int coff_y,
-                                const __nv_bfloat16 *__restrict__ dy, int ld_dy, int coff_dy, int lc8, long P,
-                                __nv_bfloat16 *__restrict__ dz) {
+// dz[p][c] = y[p][c] > 0 ? dy[p][c] : 0 (compact output), and the bias
+// gradient db[c] += sum_p dz[p][c] of the stored BF16 values: the block sums
+// its pixels per channel in shared memory, one atomic per channel and block
+// (256 threads)
+__global__ void __launch_bounds__(256) relu_bwd_kernel(const __nv_bfloat16 *__restrict__ y, int ld_y, int coff_y,
+                                                       const __nv_bfloat16 *__restrict__ dy, int ld_dy, int coff_dy,
+                                                       int lc8, long P, __nv_bfloat16 *__restrict__ dz,
+                                                       float *__restrict__ db) {
+    __shared__ float part[256][9];  // [thread][8 channels of its chunk] (+1: no bank conflicts)
     const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (P << lc8)) return;
-    const long p = i >> lc8;
-    const int c = (int)(i & ((1 << lc8) - 1)) * 8;
-    const uint4 yv = ld16(y + p * ld_y + coff_y + c), gv = ld16(dy + p * ld_dy + coff_dy + c);
-    const __nv_bfloat16 *ys = reinterpret_cast<const __nv_bfloat16 *>(&yv);
-    const __nv_bfloat16 *gs = reinterpret_cast<const __nv_bfloat16 *>(&gv);
-    uint4 o;
-    __nv_bfloat16 *os = reinterpret_cast<__nv_bfloat16 *>(&o);
+    float f[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (i < (P << lc8)) {
+        const long p = i >> lc8;
+        const int c = (int)(i & ((1 << lc8) - 1)) * 8;
+        const uint4 yv = ld16(y + p * ld_y + coff_y + c), gv = ld16(dy + p * ld_dy + coff_dy + c);
+        const __nv_bfloat16 *ys = reinterpret_cast<const __nv_bfloat16 *>(&yv);
+        const __nv_bfloat16 *gs = reinterpret_cast<const __nv_bfloat16 *>(&gv);
+        uint4 o;
+        __nv_bfloat16 *os = reinterpret_cast<__nv_bfloat16 *>(&o);
 #pragma unroll
-    for (int k = 0; k < 8; ++k) os[k] = __bfloat162float(ys[k]) > 0.f ? gs[k] : __float2bfloat16_rn(0.f);
-    st16(dz + i * 8, o);
-}
-
-// db[c] += sum_p dz[p][c]
-__global__ void bias_grad_kernel(const __nv_bfloat16 *__restrict__ dz, int C, long P, float *__restrict__ db) {
-    const int c = threadIdx.x % C;
-    const int lanes = blockDim.x / C;
-    const int sub = threadIdx.x / C;
-    float acc = 0.f;
-    for (long p = (long)blockIdx.x * lanes + sub; p < P; p += (long)gridDim.x * lanes)
-        acc += __bfloat162float(dz[p * C + c]);
-    if (sub < lanes) atomicAdd(&db[c], acc);
+        for (int k = 0; k < 8; ++k) {
+            os[k] = __bfloat162float(ys[k]) > 0.f ? gs[k] : __float2bfloat16_rn(0.f);
+            f[k] = __bfloat162float(os[k]);
+        }
+        st16(dz + i * 8, o);
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) part[threadIdx.x][k] = f[k];
+    __syncthreads();
+    // thread ch < C sums channel ch over the block: chunk c8 = ch / 8 of every
+    // pixel, i.e. threads c8, c8 + C / 8, ... (the block starts at a pixel)
+    const int C8 = 1 << lc8, C = 8 * C8;
+    if (threadIdx.x < C && (int)threadIdx.x < 256) {
+        const int c8 = threadIdx.x >> 3, k = threadIdx.x & 7;
+        float acc = 0.f;
+        for (int t = c8; t < 256; t += C8) acc += part[t][k];
+        atomicAdd(db + threadIdx.x, acc);
+    }
 }
 
 // 2x2 average pooling of an NHWC slice
@@ -578,11 +589,10 @@ int layer_bwd(oslalm_cnn *c, int L, int lvl, const __nv_bfloat16 *x, int ld_x, i
     const LayerSpec &s = kLayers[L];
     const int h = c->H >> lvl, w = c->W >> lvl;
     const long P = c->P[lvl];
-    relu_bwd_kernel<<<nb(P * s.cout / 8, 256), 256, 0, st>>>(y, ld_y, coff_y, gy, ld_gy, coff_gy, lc8(s.cout), P, c->dz);
+    relu_bwd_kernel<<<nb(P * s.cout / 8, 256), 256, 0, st>>>(y, ld_y, coff_y, gy, ld_gy, coff_gy, lc8(s.cout), P, c->dz,
+                                                             c->grad + c->off_b[L]);
     OSL_LAUNCH_CHECK("relu_bwd_kernel");
     if (int rc = wgrad(c, c->dz, s.cout, x, ld_x, coff_x, s.cin, c->grad + c->off_w[L], c->batch, h, w, st)) return rc;
-    bias_grad_kernel<<<std::min<long>(nb(P, 8), 2048), 256, 0, st>>>(c->dz, s.cout, P, c->grad + c->off_b[L]);
-    OSL_LAUNCH_CHECK("bias_grad_kernel");
     if (gx)
         return conv(c, c->dz, s.cout, 0, s.cout, c->wt[L], nullptr, gx, ld_gx, coff_gx, s.cin, c->batch, h, w, 0, st);
     return OSLALM_OK;
