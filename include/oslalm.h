@@ -369,6 +369,10 @@ int oslalm_cnn_train_step(oslalm_cnn *c, const float *x, const float *target, in
 double oslalm_cnn_flops_per_image(int height, int width);
 int oslalm_cnn_mark_timeout(oslalm_cnn *c);
 int oslalm_cnn_set_tma(oslalm_cnn *c, int enable);
+/* oslalm_cnn_launch_count: kernel launches issued so far by the network
+ * functions of this process (all networks, all devices); differences of two
+ * readings count the launches of the calls between them.  Never fails. */
+long oslalm_cnn_launch_count(void);
 
 /* ---- monitoring ----------------------------------------------------------
  * *out[host] = sqrt(sum_{mask} (x - xref)^2 / count(mask)) over the pixels

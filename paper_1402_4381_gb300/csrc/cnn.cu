@@ -7,6 +7,7 @@
 #include <math.h>
 #include <string.h>
 
+#include <atomic>
 #include <new>
 #include <vector>
 
@@ -290,6 +291,9 @@ __global__ void adam_kernel(float *__restrict__ w, const float *__restrict__ g, 
 }
 
 static inline unsigned nb(long n, int t) { return (unsigned)((n + t - 1) / t); }
+// kernel launches issued by the network functions (all networks of the process)
+static std::atomic<long> g_launches{0};
+static inline void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 // log2 of C / 8 for the 16-byte elementwise kernels (C = 32, 64, 128 or 256)
 static inline int lc8(int C) {
     int l = 0;
@@ -409,6 +413,7 @@ int conv(const oslalm_cnn *c, const __nv_bfloat16 *in, int ld_in, int coff_in, i
             opted = true;                                                                                  \
         }                                                                                                  \
         conv3x3_tma_kernel<BN><<<grid, 128, conv_tma_smem_bytes(BN), st>>>(ta, tb, a, c->err);            \
+        note_launch();                                                                                    \
     } while (0)
         switch (bn) {
             case 32: OSL_CONV_TMA(32); break;
@@ -429,6 +434,7 @@ int conv(const oslalm_cnn *c, const __nv_bfloat16 *in, int ld_in, int coff_in, i
             opted = true;                                                                                  \
         }                                                                                                  \
         conv3x3_kernel<BN><<<grid, 128, conv_smem_bytes(BN), st>>>(a, c->err);                            \
+        note_launch();                                                                                    \
     } while (0)
     switch (bn) {
         case 32: OSL_CONV(32); break;
@@ -525,6 +531,7 @@ int wgrad(const oslalm_cnn *c, const __nv_bfloat16 *dz, int cout, const __nv_bfl
             opted = true;                                                                                    \
         }                                                                                                    \
         wgrad3x3_tma_kernel<BN, GA><<<grid, 128, wgrad_tma_smem_bytes(BN, GA), st>>>(ta, tb, a, c->err);    \
+        note_launch();                                                                                      \
     } while (0)
         switch (bn * 10 + ga32) {
             case 321: OSL_WGT(32, 1); break;
@@ -560,6 +567,7 @@ int wgrad(const oslalm_cnn *c, const __nv_bfloat16 *dz, int cout, const __nv_bfl
             opted = true;                                                                                    \
         }                                                                                                    \
         wgrad3x3_tc_kernel<BN, GA><<<grid, 128, wgrad_tc_smem_bytes(BN, GA), st>>>(a, c->err);              \
+        note_launch();                                                                                      \
     } while (0)
     switch (bn * 100 + ga) {
         case 3204: OSL_WG(32, 4); break;
@@ -591,6 +599,7 @@ int layer_bwd(oslalm_cnn *c, int L, int lvl, const __nv_bfloat16 *x, int ld_x, i
     const long P = c->P[lvl];
     relu_bwd_kernel<<<nb(P * s.cout / 8, 256), 256, 0, st>>>(y, ld_y, coff_y, gy, ld_gy, coff_gy, lc8(s.cout), P, c->dz,
                                                              c->grad + c->off_b[L]);
+    note_launch();
     OSL_LAUNCH_CHECK("relu_bwd_kernel");
     if (int rc = wgrad(c, c->dz, s.cout, x, ld_x, coff_x, s.cin, c->grad + c->off_w[L], c->batch, h, w, st)) return rc;
     if (gx)
@@ -609,21 +618,27 @@ int forward_net(oslalm_cnn *c, cudaStream_t st) {
     C3(c->in0, 32, 0, 32, E0A, c->e0a, 32, 0, 32, 0);
     C3(c->e0a, 32, 0, 32, E0B, c->cat0, 96, 64, 32, 0);
     pool_kernel<<<nb(c->P[1] * 32 / 8, 256), 256, 0, st>>>(c->cat0, 96, 64, lc8(32), n, H, W, c->p0);
+    note_launch();
     C3(c->p0, 32, 0, 32, E1A, c->e1a, 64, 0, 64, 1);
     C3(c->e1a, 64, 0, 64, E1B, c->cat1, 192, 128, 64, 1);
     pool_kernel<<<nb(c->P[2] * 64 / 8, 256), 256, 0, st>>>(c->cat1, 192, 128, lc8(64), n, H / 2, W / 2, c->p1);
+    note_launch();
     C3(c->p1, 64, 0, 64, E2A, c->e2a, 128, 0, 128, 2);
     C3(c->e2a, 128, 0, 128, E2B, c->cat2, 384, 256, 128, 2);
     pool_kernel<<<nb(c->P[3] * 128 / 8, 256), 256, 0, st>>>(c->cat2, 384, 256, lc8(128), n, H / 4, W / 4, c->p2);
+    note_launch();
     C3(c->p2, 128, 0, 128, B3A, c->b3a, 256, 0, 256, 3);
     C3(c->b3a, 256, 0, 256, B3B, c->b3b, 256, 0, 256, 3);
     up_kernel<<<nb(c->P[3] * 256 / 8, 256), 256, 0, st>>>(c->b3b, lc8(256), n, H / 8, W / 8, c->cat2, 384, 0);
+    note_launch();
     C3(c->cat2, 384, 0, 384, D2A, c->d2a, 128, 0, 128, 2);
     C3(c->d2a, 128, 0, 128, D2B, c->d2b, 128, 0, 128, 2);
     up_kernel<<<nb(c->P[2] * 128 / 8, 256), 256, 0, st>>>(c->d2b, lc8(128), n, H / 4, W / 4, c->cat1, 192, 0);
+    note_launch();
     C3(c->cat1, 192, 0, 192, D1A, c->d1a, 64, 0, 64, 1);
     C3(c->d1a, 64, 0, 64, D1B, c->d1b, 64, 0, 64, 1);
     up_kernel<<<nb(c->P[1] * 64 / 8, 256), 256, 0, st>>>(c->d1b, lc8(64), n, H / 2, W / 2, c->cat0, 96, 0);
+    note_launch();
     C3(c->cat0, 96, 0, 96, D0A, c->d0a, 32, 0, 32, 0);
     C3(c->d0a, 32, 0, 32, D0B, c->d0b, 32, 0, 32, 0);
 #undef C3
@@ -638,27 +653,34 @@ int backward_net(oslalm_cnn *c, cudaStream_t st) {
     OSL_CUDA_TRY(cudaMemsetAsync(c->grad, 0, sizeof(float) * c->nparam, st));
     output_bwd_kernel<<<std::min<long>(nb(P0, 256), 1024), 256, 0, st>>>(c->dy, c->d0b, c->w32 + c->off_ow, P0, c->ga,
                                                                          c->grad + c->off_ow, c->grad + c->off_ob);
+    note_launch();
     OSL_LAUNCH_CHECK("output_bwd_kernel");
     // decoder level 0: ga = d(d0b) -> gb = d(d0a) -> g_cat0
     if ((rc = layer_bwd(c, D0B, 0, c->d0a, 32, 0, c->d0b, 32, 0, c->ga, 32, 0, c->gb, 32, 0, st))) return rc;
     if ((rc = layer_bwd(c, D0A, 0, c->cat0, 96, 0, c->d0a, 32, 0, c->gb, 32, 0, c->g_cat0, 96, 0, st))) return rc;
     up_bwd_kernel<<<nb(c->P[1] * 64 / 8, 256), 256, 0, st>>>(c->g_cat0, 96, 0, lc8(64), n, H / 2, W / 2, c->ga);  // d(d1b)
+    note_launch();
     if ((rc = layer_bwd(c, D1B, 1, c->d1a, 64, 0, c->d1b, 64, 0, c->ga, 64, 0, c->gb, 64, 0, st))) return rc;
     if ((rc = layer_bwd(c, D1A, 1, c->cat1, 192, 0, c->d1a, 64, 0, c->gb, 64, 0, c->g_cat1, 192, 0, st))) return rc;
     up_bwd_kernel<<<nb(c->P[2] * 128 / 8, 256), 256, 0, st>>>(c->g_cat1, 192, 0, lc8(128), n, H / 4, W / 4, c->ga);  // d(d2b)
+    note_launch();
     if ((rc = layer_bwd(c, D2B, 2, c->d2a, 128, 0, c->d2b, 128, 0, c->ga, 128, 0, c->gb, 128, 0, st))) return rc;
     if ((rc = layer_bwd(c, D2A, 2, c->cat2, 384, 0, c->d2a, 128, 0, c->gb, 128, 0, c->g_cat2, 384, 0, st))) return rc;
     up_bwd_kernel<<<nb(c->P[3] * 256 / 8, 256), 256, 0, st>>>(c->g_cat2, 384, 0, lc8(256), n, H / 8, W / 8, c->ga);  // d(b3b)
+    note_launch();
     if ((rc = layer_bwd(c, B3B, 3, c->b3a, 256, 0, c->b3b, 256, 0, c->ga, 256, 0, c->gb, 256, 0, st))) return rc;
     if ((rc = layer_bwd(c, B3A, 3, c->p2, 128, 0, c->b3a, 256, 0, c->gb, 256, 0, c->ga, 128, 0, st))) return rc;
     // pool 2 backward + skip gradient -> d(e2b) in gb
     pool_bwd_kernel<<<nb(c->P[2] * 128 / 8, 256), 256, 0, st>>>(c->ga, c->g_cat2, 384, 256, lc8(128), n, H / 4, W / 4, c->gb);
+    note_launch();
     if ((rc = layer_bwd(c, E2B, 2, c->e2a, 128, 0, c->cat2, 384, 256, c->gb, 128, 0, c->ga, 128, 0, st))) return rc;
     if ((rc = layer_bwd(c, E2A, 2, c->p1, 64, 0, c->e2a, 128, 0, c->ga, 128, 0, c->gb, 64, 0, st))) return rc;
     pool_bwd_kernel<<<nb(c->P[1] * 64 / 8, 256), 256, 0, st>>>(c->gb, c->g_cat1, 192, 128, lc8(64), n, H / 2, W / 2, c->ga);
+    note_launch();
     if ((rc = layer_bwd(c, E1B, 1, c->e1a, 64, 0, c->cat1, 192, 128, c->ga, 64, 0, c->gb, 64, 0, st))) return rc;
     if ((rc = layer_bwd(c, E1A, 1, c->p0, 32, 0, c->e1a, 64, 0, c->gb, 64, 0, c->ga, 32, 0, st))) return rc;
     pool_bwd_kernel<<<nb(c->P[0] * 32 / 8, 256), 256, 0, st>>>(c->ga, c->g_cat0, 96, 64, lc8(32), n, H, W, c->gb);
+    note_launch();
     if ((rc = layer_bwd(c, E0B, 0, c->e0a, 32, 0, c->cat0, 96, 64, c->gb, 32, 0, c->ga, 32, 0, st))) return rc;
     if ((rc = layer_bwd(c, E0A, 0, c->in0, 32, 0, c->e0a, 32, 0, c->ga, 32, 0, nullptr, 0, 0, st))) return rc;
     OSL_LAUNCH_CHECK("backward");
@@ -670,6 +692,7 @@ int refresh_weights(oslalm_cnn *c, cudaStream_t st) {
         const LayerSpec &s = kLayers[L];
         const long n = (long)s.cout * 9 * s.cin;
         convert_weights_kernel<<<nb(n, 256), 256, 0, st>>>(c->w32 + c->off_w[L], s.cin, s.cout, c->wb[L], c->wt[L]);
+        note_launch();
     }
     OSL_LAUNCH_CHECK("convert_weights_kernel");
     return OSLALM_OK;
@@ -695,11 +718,13 @@ int check_waits(oslalm_cnn *c) {
 int run_forward(oslalm_cnn *c, const float *x, const float *t, float s, float *y, cudaStream_t st) {
     const long P0 = c->P[0];
     pack_input_kernel<<<nb(P0 * 4, 256), 256, 0, st>>>(x, c->in0, P0, s);
+    note_launch();
     OSL_LAUNCH_CHECK("pack_input_kernel");
     if (int rc = forward_net(c, st)) return rc;
     if (t) OSL_CUDA_TRY(cudaMemsetAsync(c->loss, 0, sizeof(double), st));
     output_kernel<<<nb(P0, 256), 256, 0, st>>>(c->d0b, c->w32 + c->off_ow, c->w32 + c->off_ob, x, t, s, P0, y, c->dy,
                                                c->loss, 1.f / (float)P0);
+    note_launch();
     OSL_LAUNCH_CHECK("output_kernel");
     return OSLALM_OK;
 }
@@ -862,6 +887,8 @@ int oslalm_cnn_destroy(oslalm_cnn *c) {
     return OSLALM_OK;
 }
 
+long oslalm_cnn_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
 int oslalm_cnn_set_tma(oslalm_cnn *c, int enable) {
     clear_error();
     if (!c) return fail(OSLALM_ERR_ARG, "network handle is NULL");
@@ -944,6 +971,7 @@ int oslalm_cnn_train_step(oslalm_cnn *c, const float *x, const float *t, int n, 
     const float c1 = (float)(1.0 / (1.0 - pow(b1, (double)c->step)));
     const float c2 = (float)(1.0 / (1.0 - pow(b2, (double)c->step)));
     adam_kernel<<<nb(c->nparam, 256), 256, 0, st>>>(c->w32, c->grad, c->m, c->v, c->nparam, lr, b1, b2, 1e-8f, c1, c2);
+    note_launch();
     OSL_LAUNCH_CHECK("adam_kernel");
     if (int rc = refresh_weights(c, st)) return rc;
     if (loss) {

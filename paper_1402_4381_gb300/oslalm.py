@@ -107,6 +107,7 @@ def lib():
         "oslalm_cnn_get_params": ([_VP, _VP], i),
         "oslalm_cnn_mark_timeout": ([_VP], i),
         "oslalm_cnn_set_tma": ([_VP, ctypes.c_int], i),
+        "oslalm_cnn_launch_count": ([], ctypes.c_long),
         "oslalm_cnn_set_params": ([_VP, _VP], i),
         "oslalm_cnn_forward": ([_VP, _VP, _VP, i, ctypes.c_float, _VP], i),
         "oslalm_cnn_gradients": ([_VP, _VP, _VP, i, ctypes.c_float, _VP, ctypes.POINTER(d), _VP], i),
@@ -487,6 +488,11 @@ class WarmStartNet:
     def mark_timeout(self):
         """Set the network's timed-out mark from the host (oslalm_cnn_mark_timeout)."""
         _check(lib().oslalm_cnn_mark_timeout(self._h), "cnn_mark_timeout")
+
+    @staticmethod
+    def launch_count() -> int:
+        """Kernel launches issued so far by the network functions (oslalm_cnn_launch_count)."""
+        return int(lib().oslalm_cnn_launch_count())
 
     def set_tma(self, enable: bool):
         """Use (default) or bypass the TMA convolution (oslalm_cnn_set_tma)."""
