@@ -169,13 +169,23 @@ __global__ void __launch_bounds__(256) relu_bwd_kernel(const __nv_bfloat16 *__re
 #pragma unroll
     for (int k = 0; k < 8; ++k) part[threadIdx.x][k] = f[k];
     __syncthreads();
-    // thread ch < C sums channel ch over the block: chunk c8 = ch / 8 of every
-    // pixel, i.e. threads c8, c8 + C / 8, ... (the block starts at a pixel)
-    const int C8 = 1 << lc8, C = 8 * C8;
-    if (threadIdx.x < C && (int)threadIdx.x < 256) {
-        const int c8 = threadIdx.x >> 3, k = threadIdx.x & 7;
+    // channel ch lives in chunk c8 = ch / 8 of every pixel, i.e. in the rows of
+    // threads c8, c8 + C / 8, ... (the block starts at a pixel).  Thread t sums
+    // channel t % C over every (256 / C)-th of those rows, 8 values; then
+    // thread ch < C adds the 256 / C slices and makes the block's one atomic.
+    __shared__ float slice[256];
+    const int C8 = 1 << lc8, C = 8 * C8, S = 256 / C;
+    {
+        const int ch = threadIdx.x % C, sl = threadIdx.x / C;
+        const int c8 = ch >> 3, k = ch & 7;
         float acc = 0.f;
-        for (int t = c8; t < 256; t += C8) acc += part[t][k];
+        for (int j = sl; j < 256 / C8; j += S) acc += part[c8 + j * C8][k];
+        slice[threadIdx.x] = acc;  // = slice[sl * C + ch]
+    }
+    __syncthreads();
+    if ((int)threadIdx.x < C) {
+        float acc = 0.f;
+        for (int sl = 0; sl < S; ++sl) acc += slice[sl * C + threadIdx.x];
         atomicAdd(db + threadIdx.x, acc);
     }
 }
