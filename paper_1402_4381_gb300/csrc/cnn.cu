@@ -397,6 +397,25 @@ bool conv_tensor_maps(const __nv_bfloat16 *in, int ld_in, int coff_in, int cin, 
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// Tensor maps of the halo convolution (32 input channels, width a multiple of
+// 128): the input as (channel, column, row, image) with boxes of 32 channels x
+// 130 pixels x 1 row, the weights as for conv_tensor_maps.
+bool conv_halo_maps(const __nv_bfloat16 *in, int ld_in, int coff_in, int cin, const __nv_bfloat16 *w, int cout,
+                    int n, int h, int wd, int bn, CUtensorMap *ta, CUtensorMap *tb) {
+    if (cin != kBK || wd % kBM) return false;
+    // the weights' map and the alignment checks are those of the row-tile path
+    if (!conv_tensor_maps(in, ld_in, coff_in, cin, w, cout, n, h, wd, bn, ta, tb)) return false;
+    PFN_cuTensorMapEncodeTiled_v12000 enc = encode_tiled();
+    const cuuint64_t es = 2;
+    const cuuint64_t gdA[4] = {(cuuint64_t)cin, (cuuint64_t)wd, (cuuint64_t)h, (cuuint64_t)n};
+    const cuuint64_t gsA[3] = {ld_in * es, (cuuint64_t)wd * ld_in * es, (cuuint64_t)h * wd * ld_in * es};
+    const cuuint32_t boxA[4] = {(cuuint32_t)kBK, (cuuint32_t)(kBM + 2), 1, 1};
+    const cuuint32_t one[4] = {1, 1, 1, 1};
+    return enc(ta, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<__nv_bfloat16 *>(in + coff_in), gdA, gsA, boxA,
+               one, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 int conv(const oslalm_cnn *c, const __nv_bfloat16 *in, int ld_in, int coff_in, int cin, const __nv_bfloat16 *w,
          const float *bias, __nv_bfloat16 *out, int ld_out, int coff_out, int cout, int n, int h, int wd, int relu,
          cudaStream_t st) {
@@ -413,6 +432,28 @@ int conv(const oslalm_cnn *c, const __nv_bfloat16 *in, int ld_in, int coff_in, i
     if (bn < 32 || cin % kBK) return fail(OSLALM_ERR_ARG, "convolution needs channel counts that are multiples of 32");
     dim3 grid(nb(P, kBM), cout / bn);
     CUtensorMap ta, tb;
+    if (c->use_tma && conv_halo_maps(in, ld_in, coff_in, cin, w, cout, n, h, wd, bn, &ta, &tb)) {
+#define OSL_CONV_HALO(BN)                                                                                  \
+    do {                                                                                                   \
+        static bool opted = false;                                                                         \
+        if (!opted) {                                                                                      \
+            OSL_CUDA_TRY(cudaFuncSetAttribute(conv3x3_halo_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                              conv_halo_smem_bytes(BN)));                                  \
+            opted = true;                                                                                  \
+        }                                                                                                  \
+        conv3x3_halo_kernel<BN><<<grid, 128, conv_halo_smem_bytes(BN), st>>>(ta, tb, a, c->err);          \
+        note_launch();                                                                                     \
+    } while (0)
+        switch (bn) {
+            case 32: OSL_CONV_HALO(32); break;
+            case 64: OSL_CONV_HALO(64); break;
+            case 128: OSL_CONV_HALO(128); break;
+            default: OSL_CONV_HALO(256); break;
+        }
+#undef OSL_CONV_HALO
+        OSL_LAUNCH_CHECK("conv3x3_halo_kernel");
+        return OSLALM_OK;
+    }
     if (c->use_tma && conv_tensor_maps(in, ld_in, coff_in, cin, w, cout, n, h, wd, bn, &ta, &tb)) {
 #define OSL_CONV_TMA(BN)                                                                                   \
     do {                                                                                                   \

@@ -458,6 +458,100 @@ __global__ void __launch_bounds__(128) conv3x3_tma_kernel(const __grid_constant_
     if (warp == 0) tc::tmem_dealloc(taddr, BN);
 }
 
+// The convolution of a 32-channel input on a level whose width is a multiple
+// of 128, with each input row read once for its three horizontal taps: for
+// tap row dy the box of 32 channels x 130 pixels x 1 row at (0, x0 - 1,
+// y0 + dy, image) (the map's zero fill is the padding at both ends) lands as
+// 130 rows of 64 bytes in the 64-byte swizzle, and the MMAs of taps dx = -1, 0,
+// +1 read it from 0, 64 and 128 bytes on (one pixel per 64 bytes; the swizzle
+// follows the shared-memory address, as the TMA wrote it).  The three rows and
+// the nine weight tiles are all issued at once; the MMAs run in tap order, as
+// in conv3x3_tma_kernel, so the results are the same bits.
+constexpr int kHaloSlot = 9216;  // 130 x 64 bytes, rounded up to 1 KB
+__host__ __device__ constexpr int conv_halo_smem_bytes(int bn) { return 1024 + 3 * (kHaloSlot + 3 * bn * 64); }
+
+template <int BN>
+__global__ void __launch_bounds__(128) conv3x3_halo_kernel(const __grid_constant__ CUtensorMap tmA,
+                                                           const __grid_constant__ CUtensorMap tmB, ConvArgs a,
+                                                           int *err) {
+    extern __shared__ __align__(1024) unsigned char sm[];
+    constexpr int B_TAP = BN * 64, S_BYTES = kHaloSlot + 3 * B_TAP;
+    uint64_t *full = reinterpret_cast<uint64_t *>(sm);
+    uint64_t *done_bar = full + 3;
+    uint32_t *s_taddr = reinterpret_cast<uint32_t *>(done_bar + 1);
+    unsigned char *stages = sm + 1024;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    if (smem_u32(stages) & 1023u) {  // the swizzled rows need 1 KB aligned buffers
+        if (tid == 0) atomicOr(err, 2);
+        return;
+    }
+    const long P = (long)a.n * a.h * a.wd;
+    const long p0 = (long)blockIdx.x * kBM;
+    const int co0 = blockIdx.y * BN;
+    if (warp == 0) tc::tmem_alloc(s_taddr, BN);
+    if (tid < 4) tc::mbar_init(&full[tid], 1);  // full[0..3) and done_bar
+    tc::fence_barrier_init();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t taddr = *s_taddr;
+    bool ok = true;
+    if (tid == 0) {
+        tma::prefetch_map(&tmA);
+        tma::prefetch_map(&tmB);
+        const long hw = (long)a.h * a.wd;
+        const int img = (int)(p0 / hw);
+        const int rem = (int)(p0 - (long)img * hw);
+        const int y0 = rem / a.wd, x0 = rem - (rem / a.wd) * a.wd;
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            unsigned char *A = stages + r * S_BYTES, *B = A + kHaloSlot;
+            tma::arrive_expect_tx(&full[r], (uint32_t)(130 * 64 + 3 * B_TAP));
+            tma::load_4d(A, &tmA, 0, x0 - 1, y0 + r - 1, img, &full[r]);
+#pragma unroll
+            for (int d = 0; d < 3; ++d) tma::load_2d(B + d * B_TAP, &tmB, (3 * r + d) * kBK, co0, &full[r]);
+        }
+        int waited = 0;
+        for (int r = 0; r < 3 && ok; ++r) {
+            if (!tc::mbar_wait(&full[r], 0)) {
+                ok = false;
+                break;
+            }
+            waited = r + 1;
+            tc::fence_after_sync();
+            const unsigned char *A = stages + r * S_BYTES, *B = A + kHaloSlot;
+#pragma unroll
+            for (int d = 0; d < 3; ++d)
+#pragma unroll
+                for (int kh = 0; kh < kBK / 16; ++kh)
+                    tc::mma_bf16(taddr, tc::smem_desc_sw64(A + d * 64 + kh * 32),
+                                 tc::smem_desc_sw64(B + d * B_TAP + kh * 32), tc::idesc_bf16(kBM, BN),
+                                 (r > 0 || d > 0 || kh > 0) ? 1u : 0u);
+        }
+        if (waited > 0) tc::mma_commit(done_bar);
+        if (ok) ok = tc::mbar_wait(done_bar, 0);
+        if (!ok) {
+            // let the transfers land and the committed MMAs finish (bounded)
+            // before the block's memory is released
+            atomicOr(err, 1);
+            for (int r = waited; r < 3; ++r) tc::mbar_wait(&full[r], 0);
+            if (waited > 0) tc::mbar_wait(done_bar, 0);
+        }
+    }
+    if (!__syncthreads_and(ok)) {
+        tc::fence_before_sync();
+        __syncthreads();
+        if (warp == 0) tc::tmem_dealloc(taddr, BN);
+        return;
+    }
+    tc::fence_after_sync();
+    conv_epilogue<BN>(a, taddr, p0, co0, P);
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(taddr, BN);
+}
+
+
 struct WgradArgs {
     const __nv_bfloat16 *dz;  // [P][cout] (ld_dz, coff_dz)
     int ld_dz, coff_dz, cout;
