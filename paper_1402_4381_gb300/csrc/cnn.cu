@@ -397,12 +397,12 @@ bool conv_tensor_maps(const __nv_bfloat16 *in, int ld_in, int coff_in, int cin, 
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-// Tensor maps of the halo convolution (32 input channels, width a multiple of
-// 128): the input as (channel, column, row, image) with boxes of 32 channels x
-// 130 pixels x 1 row, the weights as for conv_tensor_maps.
+// Tensor maps of the halo convolution (width a multiple of 128): the input as
+// (channel, column, row, image) with boxes of 32 channels x 130 pixels x 1
+// row, the weights as for conv_tensor_maps.
 bool conv_halo_maps(const __nv_bfloat16 *in, int ld_in, int coff_in, int cin, const __nv_bfloat16 *w, int cout,
                     int n, int h, int wd, int bn, CUtensorMap *ta, CUtensorMap *tb) {
-    if (cin != kBK || wd % kBM) return false;
+    if (cin % kBK || wd % kBM) return false;
     // the weights' map and the alignment checks are those of the row-tile path
     if (!conv_tensor_maps(in, ld_in, coff_in, cin, w, cout, n, h, wd, bn, ta, tb)) return false;
     PFN_cuTensorMapEncodeTiled_v12000 enc = encode_tiled();

@@ -234,7 +234,10 @@ __global__ void __launch_bounds__(128) conv3x3_kernel(ConvArgs a, int *err) {
         pin[q] = a.in + (in ? p : 0) * a.ld_in + a.coff_in + ch * 8;
     }
     auto load_stage = [&](int ks, int buf) {
-        const int tap = ks / csteps, ci0 = (ks % csteps) * kBK;
+        // K order: tap row dy, then channel step, then dx (the order of the
+        // halo kernel, which reads a row's three taps from one load)
+        const int dyi = ks / (3 * csteps), rem = ks - dyi * 3 * csteps;
+        const int cs = rem / 3, tap = dyi * 3 + (rem - cs * 3), ci0 = cs * kBK;
         const int dy = tap / 3 - 1, dx = tap % 3 - 1;
         const long shift = ((long)dy * a.wd + dx) * a.ld_in + ci0;
         unsigned char *A = sA + buf * A_BYTES;
@@ -397,18 +400,22 @@ __global__ void __launch_bounds__(128) conv3x3_tma_kernel(const __grid_constant_
         const int rem = (int)(p0 - (long)img * hw);
         const int y0 = rem / a.wd, x0 = rem - (rem / a.wd) * a.wd;
         int issued = 0, done = 0;
-        int tap_i = 0, cs_i = 0;  // tap and channel step of the next stage to issue
+        // K order: tap row dy, then channel step, then dx (as in conv3x3_kernel)
+        int dy_i = 0, cs_i = 0, dx_i = 0;  // of the next stage to issue
         auto issue = [&]() {
             const int s = issued++;
             unsigned char *A = stages + (s % NS) * S_BYTES, *B = A + A_BYTES;
             uint64_t *fb = &full[s % NS];
-            const int dy = tap_i / 3 - 1, dx = tap_i % 3 - 1, ci0 = cs_i * kBK;
+            const int tap = dy_i * 3 + dx_i, dy = dy_i - 1, dx = dx_i - 1, ci0 = cs_i * kBK;
             tma::arrive_expect_tx(fb, (uint32_t)S_BYTES);
             tma::load_4d(A, &tmA, ci0, x0 + dx, y0 + dy, img, fb);
-            tma::load_2d(B, &tmB, tap_i * a.cin + ci0, co0, fb);
-            if (++cs_i == csteps) {
-                cs_i = 0;
-                ++tap_i;
+            tma::load_2d(B, &tmB, tap * a.cin + ci0, co0, fb);
+            if (++dx_i == 3) {
+                dx_i = 0;
+                if (++cs_i == csteps) {
+                    cs_i = 0;
+                    ++dy_i;
+                }
             }
         };
         while (issued < NS && issued < nk) issue();
@@ -458,27 +465,33 @@ __global__ void __launch_bounds__(128) conv3x3_tma_kernel(const __grid_constant_
     if (warp == 0) tc::tmem_dealloc(taddr, BN);
 }
 
-// The convolution of a 32-channel input on a level whose width is a multiple
-// of 128, with each input row read once for its three horizontal taps: for
-// tap row dy the box of 32 channels x 130 pixels x 1 row at (0, x0 - 1,
-// y0 + dy, image) (the map's zero fill is the padding at both ends) lands as
-// 130 rows of 64 bytes in the 64-byte swizzle, and the MMAs of taps dx = -1, 0,
-// +1 read it from 0, 64 and 128 bytes on (one pixel per 64 bytes; the swizzle
-// follows the shared-memory address, as the TMA wrote it).  The three rows and
-// the nine weight tiles are all issued at once; the MMAs run in tap order, as
-// in conv3x3_tma_kernel, so the results are the same bits.
+// The convolution on a level whose width is a multiple of 128, with each
+// input row read once for its three horizontal taps.  A stage is one tap row
+// dy and one 32-channel step: the box of 32 channels x 130 pixels x 1 row at
+// (ci, x0 - 1, y0 + dy, image) (the map's zero fill is the padding at both
+// ends) lands as 130 rows of 64 bytes in the 64-byte swizzle, and the MMAs of
+// taps dx = -1, 0, +1 read it from 0, 64 and 128 bytes on (one pixel per 64
+// bytes; the tensor cores apply the swizzle from the shared-memory address,
+// as the TMA wrote it), with the stage's three weight tiles.  Three stages in
+// flight, refilled as in conv3x3_tma_kernel; the MMAs run in the K order of
+// the other convolution kernels (dy, channel step, dx), so the results are
+// the same bits.
 constexpr int kHaloSlot = 9216;  // 130 x 64 bytes, rounded up to 1 KB
-__host__ __device__ constexpr int conv_halo_smem_bytes(int bn) { return 1024 + 3 * (kHaloSlot + 3 * bn * 64); }
+constexpr int kHaloStages = 3;
+__host__ __device__ constexpr int conv_halo_smem_bytes(int bn) {
+    return 1024 + kHaloStages * (kHaloSlot + 3 * bn * 64);
+}
 
 template <int BN>
 __global__ void __launch_bounds__(128) conv3x3_halo_kernel(const __grid_constant__ CUtensorMap tmA,
                                                            const __grid_constant__ CUtensorMap tmB, ConvArgs a,
                                                            int *err) {
     extern __shared__ __align__(1024) unsigned char sm[];
-    constexpr int B_TAP = BN * 64, S_BYTES = kHaloSlot + 3 * B_TAP;
+    constexpr int NS = kHaloStages, B_TAP = BN * 64, S_BYTES = kHaloSlot + 3 * B_TAP;
+    constexpr uint32_t TX = 130 * 64 + 3 * B_TAP;
     uint64_t *full = reinterpret_cast<uint64_t *>(sm);
-    uint64_t *done_bar = full + 3;
-    uint32_t *s_taddr = reinterpret_cast<uint32_t *>(done_bar + 1);
+    uint64_t *empty = full + NS;
+    uint32_t *s_taddr = reinterpret_cast<uint32_t *>(empty + NS);
     unsigned char *stages = sm + 1024;
     const int tid = threadIdx.x, warp = tid >> 5;
     if (smem_u32(stages) & 1023u) {  // the swizzled rows need 1 KB aligned buffers
@@ -488,8 +501,10 @@ __global__ void __launch_bounds__(128) conv3x3_halo_kernel(const __grid_constant
     const long P = (long)a.n * a.h * a.wd;
     const long p0 = (long)blockIdx.x * kBM;
     const int co0 = blockIdx.y * BN;
+    const int csteps = a.cin / kBK;
+    const int nk = 3 * csteps;
     if (warp == 0) tc::tmem_alloc(s_taddr, BN);
-    if (tid < 4) tc::mbar_init(&full[tid], 1);  // full[0..3) and done_bar
+    if (tid < 2 * NS) tc::mbar_init(&full[tid], 1);  // full[0..NS) and empty[0..NS)
     tc::fence_barrier_init();
     tc::fence_before_sync();
     __syncthreads();
@@ -503,39 +518,56 @@ __global__ void __launch_bounds__(128) conv3x3_halo_kernel(const __grid_constant
         const int img = (int)(p0 / hw);
         const int rem = (int)(p0 - (long)img * hw);
         const int y0 = rem / a.wd, x0 = rem - (rem / a.wd) * a.wd;
+        int issued = 0, done = 0;
+        int dy_i = 0, cs_i = 0;  // tap row and channel step of the next stage to issue
+        auto issue = [&]() {
+            const int s = issued++;
+            unsigned char *A = stages + (s % NS) * S_BYTES, *B = A + kHaloSlot;
+            uint64_t *fb = &full[s % NS];
+            const int ci0 = cs_i * kBK;
+            tma::arrive_expect_tx(fb, TX);
+            tma::load_4d(A, &tmA, ci0, x0 - 1, y0 + dy_i - 1, img, fb);
 #pragma unroll
-        for (int r = 0; r < 3; ++r) {
-            unsigned char *A = stages + r * S_BYTES, *B = A + kHaloSlot;
-            tma::arrive_expect_tx(&full[r], (uint32_t)(130 * 64 + 3 * B_TAP));
-            tma::load_4d(A, &tmA, 0, x0 - 1, y0 + r - 1, img, &full[r]);
-#pragma unroll
-            for (int d = 0; d < 3; ++d) tma::load_2d(B + d * B_TAP, &tmB, (3 * r + d) * kBK, co0, &full[r]);
-        }
-        int waited = 0;
-        for (int r = 0; r < 3 && ok; ++r) {
-            if (!tc::mbar_wait(&full[r], 0)) {
+            for (int d = 0; d < 3; ++d) tma::load_2d(B + d * B_TAP, &tmB, (3 * dy_i + d) * a.cin + ci0, co0, fb);
+            if (++cs_i == csteps) {
+                cs_i = 0;
+                ++dy_i;
+            }
+        };
+        while (issued < NS && issued < nk) issue();
+        for (int ks = 0; ks < nk; ++ks) {
+            const int buf = ks % NS;
+            if (!tc::mbar_wait(&full[buf], (ks / NS) & 1)) {
                 ok = false;
                 break;
             }
-            waited = r + 1;
             tc::fence_after_sync();
-            const unsigned char *A = stages + r * S_BYTES, *B = A + kHaloSlot;
+            const unsigned char *A = stages + buf * S_BYTES, *B = A + kHaloSlot;
 #pragma unroll
             for (int d = 0; d < 3; ++d)
 #pragma unroll
                 for (int kh = 0; kh < kBK / 16; ++kh)
                     tc::mma_bf16(taddr, tc::smem_desc_sw64(A + d * 64 + kh * 32),
                                  tc::smem_desc_sw64(B + d * B_TAP + kh * 32), tc::idesc_bf16(kBM, BN),
-                                 (r > 0 || d > 0 || kh > 0) ? 1u : 0u);
+                                 (ks > 0 || d > 0 || kh > 0) ? 1u : 0u);
+            tc::mma_commit(&empty[buf]);
+            done = ks + 1;
+            // refill the stage of step ks - 1: its MMAs precede this step's
+            if (ks >= 1 && issued < nk) {
+                if (!tc::mbar_wait(&empty[(ks - 1) % NS], ((ks - 1) / NS) & 1)) {
+                    ok = false;
+                    break;
+                }
+                issue();
+            }
         }
-        if (waited > 0) tc::mma_commit(done_bar);
-        if (ok) ok = tc::mbar_wait(done_bar, 0);
+        if (ok && nk > 0) ok = tc::mbar_wait(&empty[(nk - 1) % NS], ((nk - 1) / NS) & 1);
         if (!ok) {
-            // let the transfers land and the committed MMAs finish (bounded)
-            // before the block's memory is released
+            // let the issued transfers land and the committed MMAs finish
+            // (each wait bounded) before the block's memory is released
             atomicOr(err, 1);
-            for (int r = waited; r < 3; ++r) tc::mbar_wait(&full[r], 0);
-            if (waited > 0) tc::mbar_wait(done_bar, 0);
+            for (int s = done; s < issued; ++s) tc::mbar_wait(&full[s % NS], (s / NS) & 1);
+            if (done > 0) tc::mbar_wait(&empty[(done - 1) % NS], ((done - 1) / NS) & 1);
         }
     }
     if (!__syncthreads_and(ok)) {
@@ -550,7 +582,6 @@ __global__ void __launch_bounds__(128) conv3x3_halo_kernel(const __grid_constant
     __syncthreads();
     if (warp == 0) tc::tmem_dealloc(taddr, BN);
 }
-
 
 struct WgradArgs {
     const __nv_bfloat16 *dz;  // [P][cout] (ld_dz, coff_dz)
