@@ -539,6 +539,24 @@ bool wgrad_tensor_maps(const __nv_bfloat16 *dz, int ld_dz, int coff_dz, int cout
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// Tensor maps of the three-tap weight gradient (width a multiple of 64): dz as
+// for wgrad_tensor_maps, the input slice with boxes of 32 channels x 66 pixels
+// x 1 row (the halo row of a 64-pixel stage).
+bool wgrad_halo_maps(const __nv_bfloat16 *dz, int ld_dz, int coff_dz, int cout, const __nv_bfloat16 *x, int ld_x,
+                     int coff_x, int cin, int n, int h, int wd, CUtensorMap *ta, CUtensorMap *tb) {
+    if (wd % kWgBK) return false;
+    if (!wgrad_tensor_maps(dz, ld_dz, coff_dz, cout, x, ld_x, coff_x, cin, n, h, wd, ta, tb)) return false;
+    PFN_cuTensorMapEncodeTiled_v12000 enc = encode_tiled();
+    const cuuint64_t es = 2;
+    const cuuint64_t gdB[4] = {(cuuint64_t)cin, (cuuint64_t)wd, (cuuint64_t)h, (cuuint64_t)n};
+    const cuuint64_t gsB[3] = {ld_x * es, (cuuint64_t)wd * ld_x * es, (cuuint64_t)h * wd * ld_x * es};
+    const cuuint32_t boxB[4] = {32, (cuuint32_t)(kWgBK + 2), 1, 1};
+    const cuuint32_t one[4] = {1, 1, 1, 1};
+    return enc(tb, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<__nv_bfloat16 *>(x + coff_x), gdB, gsB, boxB, one,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 int wgrad(const oslalm_cnn *c, const __nv_bfloat16 *dz, int cout, const __nv_bfloat16 *x, int ld_x, int coff_x,
           int cin, float *dw, int n, int h, int wd, cudaStream_t st) {
     WgradArgs a;
@@ -568,6 +586,46 @@ int wgrad(const oslalm_cnn *c, const __nv_bfloat16 *dz, int cout, const __nv_bfl
     };
     CUtensorMap ta, tb;
     const int ga32 = std::min(4, cout / 32);
+    if (c->use_tma && cout % 32 == 0 && ga32 != 3 && bn <= 128 &&
+        wgrad_halo_maps(dz, cout, 0, cout, x, ld_x, coff_x, cin, n, h, wd, &ta, &tb)) {
+        // the three horizontal taps of a tap row per block
+        const int smem = wgrad_halo_smem_bytes(bn, ga32);
+        int occ = std::min(smem_sm / (smem + 1024), std::min(512 / wgrad_halo_tmem_cols(bn), 16));
+        if (occ < 1) occ = 1;
+        const long tiles = (long)((cout + 127) / 128) * 3 * (cin / bn);
+        long splits = ((long)sms * occ) / tiles;
+        if (splits < 1) splits = 1;
+        long per = (P + splits - 1) / splits;
+        per = ((per + kWgBK - 1) / kWgBK) * kWgBK;
+        a.pix_per_block = (int)per;
+        const dim3 grid((cout + 127) / 128, 3 * (cin / bn), (unsigned)((P + per - 1) / per));
+#define OSL_WGH(BN, GA)                                                                                      \
+    do {                                                                                                     \
+        static bool opted = false;                                                                           \
+        if (!opted) {                                                                                        \
+            OSL_CUDA_TRY(cudaFuncSetAttribute(wgrad3x3_halo_kernel<BN, GA>,                                  \
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize,                   \
+                                              wgrad_halo_smem_bytes(BN, GA)));                               \
+            opted = true;                                                                                    \
+        }                                                                                                    \
+        wgrad3x3_halo_kernel<BN, GA><<<grid, 128, wgrad_halo_smem_bytes(BN, GA), st>>>(ta, tb, a, c->err);  \
+        note_launch();                                                                                       \
+    } while (0)
+        switch (bn * 10 + ga32) {
+            case 321: OSL_WGH(32, 1); break;
+            case 322: OSL_WGH(32, 2); break;
+            case 324: OSL_WGH(32, 4); break;
+            case 641: OSL_WGH(64, 1); break;
+            case 642: OSL_WGH(64, 2); break;
+            case 644: OSL_WGH(64, 4); break;
+            case 1281: OSL_WGH(128, 1); break;
+            case 1282: OSL_WGH(128, 2); break;
+            default: OSL_WGH(128, 4); break;
+        }
+#undef OSL_WGH
+        OSL_LAUNCH_CHECK("wgrad3x3_halo_kernel");
+        return OSLALM_OK;
+    }
     if (c->use_tma && cout % 32 == 0 && ga32 != 3 &&
         wgrad_tensor_maps(dz, cout, 0, cout, x, ld_x, coff_x, cin, n, h, wd, &ta, &tb)) {
         const int smem = wgrad_tma_smem_bytes(bn, ga32);

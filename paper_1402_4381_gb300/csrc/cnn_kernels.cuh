@@ -930,5 +930,137 @@ __global__ void __launch_bounds__(128) wgrad3x3_tma_kernel(const __grid_constant
     if (warp == 0) tc::tmem_dealloc(taddr, BN);
 }
 
+// The weight gradient of the three horizontal taps of one tap row at once, on
+// levels whose width is a multiple of 64: a stage is 64 pixels of one image
+// row; dz as in wgrad3x3_tma_kernel, the input as a halo row of 66 pixels
+// (x0 - 1 .. x0 + 64 of row y0 + dy, zero outside the image) per 32-channel
+// atom, so that the tap dx reads it from (dx + 1) x 64 bytes on (one pixel per
+// 64-byte row of the swizzled tile).  Three accumulators of BN columns in
+// tensor memory, one per tap; both operands are loaded once for the three.
+constexpr int kWgHaloAtom = 5120;  // 66 x 64 bytes, rounded up to 1 KB
+__host__ __device__ constexpr int wgrad_halo_stage_bytes(int bn, int ga32) {
+    return ga32 * kWgTmaAtom + (bn / 32) * kWgHaloAtom;
+}
+__host__ __device__ constexpr int wgrad_halo_smem_bytes(int bn, int ga32) {
+    return 1024 + kWgTmaStages * wgrad_halo_stage_bytes(bn, ga32) + 4 * kWgTmaAtom;
+}
+__host__ __device__ constexpr int wgrad_halo_tmem_cols(int bn) { return bn <= 32 ? 128 : (bn <= 64 ? 256 : 512); }
+
+template <int BN, int GA32>
+__global__ void __launch_bounds__(128) wgrad3x3_halo_kernel(const __grid_constant__ CUtensorMap tmA,
+                                                            const __grid_constant__ CUtensorMap tmB, WgradArgs a,
+                                                            int *err) {
+    extern __shared__ __align__(1024) unsigned char sm[];
+    constexpr int NS = kWgTmaStages, BM = 128, BK = kWgBK, TC = wgrad_halo_tmem_cols(BN);
+    constexpr int A_BYTES = GA32 * kWgTmaAtom, S_BYTES = wgrad_halo_stage_bytes(BN, GA32);
+    constexpr uint32_t TX = A_BYTES + (BN / 32) * 66 * 64;
+    static_assert(3 * BN <= 512, "three accumulators");
+    uint64_t *full = reinterpret_cast<uint64_t *>(sm);
+    uint64_t *empty = full + NS;
+    uint32_t *s_taddr = reinterpret_cast<uint32_t *>(empty + NS);
+    unsigned char *stages = sm + 1024;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (smem_u32(stages) & 1023u) {
+        if (tid == 0) atomicOr(err, 2);
+        return;
+    }
+    const long P = (long)a.n * a.h * a.wd;
+    const int co0 = blockIdx.x * BM;
+    const int dyi = blockIdx.y / (a.cin / BN);
+    const int ci0 = (blockIdx.y % (a.cin / BN)) * BN;
+    const long pbeg = (long)blockIdx.z * a.pix_per_block;
+    const long pend = pbeg + a.pix_per_block < P ? pbeg + a.pix_per_block : P;
+    const int nk = pend > pbeg ? (int)((pend - pbeg) / BK) : 0;
+    if (warp == 0) tc::tmem_alloc(s_taddr, TC);
+    if (tid < 2 * NS) tc::mbar_init(&full[tid], 1);
+    tc::fence_barrier_init();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t taddr = *s_taddr;
+    bool ok = true;
+    if (tid == 0) {
+        tma::prefetch_map(&tmA);
+        tma::prefetch_map(&tmB);
+        const long hw = (long)a.h * a.wd;
+        int issued = 0, done = 0;
+        auto issue = [&]() {
+            const int s = issued++;
+            const long pb = pbeg + (long)s * BK;
+            const int img = (int)(pb / hw);
+            const int rem = (int)(pb - (long)img * hw);
+            const int y0 = rem / a.wd, x0 = rem - (rem / a.wd) * a.wd;
+            unsigned char *A = stages + (s % NS) * S_BYTES, *B = A + A_BYTES;
+            uint64_t *fb = &full[s % NS];
+            tma::arrive_expect_tx(fb, TX);
+#pragma unroll
+            for (int g = 0; g < GA32; ++g) tma::load_2d(A + g * kWgTmaAtom, &tmA, co0 + 32 * g, (int)pb, fb);
+#pragma unroll
+            for (int g = 0; g < BN / 32; ++g)
+                tma::load_4d(B + g * kWgHaloAtom, &tmB, ci0 + 32 * g, x0 - 1, y0 + dyi - 1, img, fb);
+        };
+        while (issued < NS && issued < nk) issue();
+        constexpr uint32_t idesc = tc::idesc_bf16(BM, BN) | (1u << 15) | (1u << 16);  // A and B MN-major
+        for (int ks = 0; ks < nk; ++ks) {
+            const int buf = ks % NS;
+            if (!tc::mbar_wait(&full[buf], (ks / NS) & 1)) {
+                ok = false;
+                break;
+            }
+            tc::fence_after_sync();
+            const unsigned char *A = stages + buf * S_BYTES, *B = A + A_BYTES;
+#pragma unroll
+            for (int d = 0; d < 3; ++d)
+#pragma unroll
+                for (int kh = 0; kh < BK / 16; ++kh)  // 16 pixels (two 8-row groups) per MMA
+                    tc::mma_bf16(taddr + (uint32_t)(d * BN), smem_desc_mn_sw64(A + kh * 1024, kWgTmaAtom),
+                                 smem_desc_mn_sw64(B + d * 64 + kh * 1024, kWgHaloAtom), idesc,
+                                 (ks > 0 || kh > 0) ? 1u : 0u);
+            tc::mma_commit(&empty[buf]);
+            done = ks + 1;
+            if (ks >= 1 && issued < nk) {
+                if (!tc::mbar_wait(&empty[(ks - 1) % NS], ((ks - 1) / NS) & 1)) {
+                    ok = false;
+                    break;
+                }
+                issue();
+            }
+        }
+        if (ok && nk > 0) ok = tc::mbar_wait(&empty[(nk - 1) % NS], ((nk - 1) / NS) & 1);
+        if (!ok) {
+            atomicOr(err, 1);
+            for (int s = done; s < issued; ++s) tc::mbar_wait(&full[s % NS], (s / NS) & 1);
+            if (done > 0) tc::mbar_wait(&empty[(done - 1) % NS], ((done - 1) / NS) & 1);
+        }
+    }
+    if (!__syncthreads_and(ok)) {
+        tc::fence_before_sync();
+        __syncthreads();
+        if (warp == 0) tc::tmem_dealloc(taddr, TC);
+        return;
+    }
+    tc::fence_after_sync();
+    if (nk > 0 && co0 + warp * 32 < a.cout) {
+        const int co = co0 + warp * 32 + lane;  // this thread's accumulator row (tensor-memory lane)
+#pragma unroll 1
+        for (int d = 0; d < 3; ++d) {
+            const int tap = dyi * 3 + d;
+#pragma unroll 1
+            for (int c = 0; c < BN; c += 8) {
+                float v[8];
+                tc::tmem_ld8(taddr + ((uint32_t)(warp * 32) << 16) + (uint32_t)(d * BN + c), v);
+                if (co < a.cout) {
+                    float *dd = a.dw + ((long)co * 9 + tap) * a.cin + ci0 + c;
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) atomicAdd(dd + i, v[i]);
+                }
+            }
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(taddr, TC);
+}
+
 }  // namespace cnn
 }  // namespace oslalm
