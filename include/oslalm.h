@@ -350,11 +350,17 @@ int oslalm_batch_shape_info(int shape, int *tile_x, int *tile_y, int *lanes);
  *   convolution whose wait ran out would (synchronous), so that callers can
  *   test their handling of OSLALM_ERR_TIMEOUT without a device fault.
  *   Errors: ARG, CUDA.
- * oslalm_cnn_set_tma: enable (default) or disable the TMA convolution, used
+ * oslalm_cnn_set_tma: enable (default) or disable the TMA forms of the
+ *   convolutions and weight gradients.  Convolutions take their tiles by TMA
  *   where a level's 128-pixel blocks are whole rows or row segments (width a
- *   multiple of 128, or 128 / width rows with the height a multiple of that);
- *   disabled, every convolution stages its tiles with cp.async.  Both run
- *   the same MMAs in the same order, so the results are identical.  Errors: ARG. */
+ *   multiple of 128, or 128 / width rows with the height a multiple of that),
+ *   and on widths that are a multiple of 128 load each input row once for its
+ *   three horizontal taps; weight gradients likewise for 64-pixel stages
+ *   (three taps per block on widths that are a multiple of 64).  Disabled,
+ *   every kernel stages its tiles with cp.async.  The convolutions run the
+ *   same MMAs in the same order on every path, so their outputs are
+ *   identical; the weight gradients agree to the rounding of their FP32
+ *   atomic sums.  Errors: ARG. */
 typedef struct oslalm_cnn oslalm_cnn;
 long oslalm_cnn_param_count(void);
 int oslalm_cnn_create(int batch, int height, int width, unsigned long long seed, oslalm_cnn **out);
