@@ -10,10 +10,18 @@
 //   channels, double-buffered cp.async staging into the core-matrix layout,
 //   MMAs issued by one thread and tracked by mbarriers.  With transposed,
 //   tap-flipped weights the same kernel computes the data gradient.
+// conv3x3_tma_kernel / conv3x3_halo_kernel: the same with the tiles brought
+//   in by TMA as 64-byte swizzled rows (whole-row blocks); the halo form loads
+//   each input row once with a one-pixel halo for its three horizontal taps.
+//   All three take the K steps in one order (tap row, channel step, tap
+//   column), so they give the same bits.
 // wgrad3x3_tc_kernel: dW[co][tap][ci] = sum_p dz[p][co] x[p + shift(tap)][ci]
 //   on the tcgen05 tensor cores with both operands MN-major (pixel-major
 //   activations staged as they are), split over pixel ranges, partial tiles
 //   added with FP32 atomics.
+// wgrad3x3_tma_kernel / wgrad3x3_halo_kernel: the same by TMA; the halo form
+//   computes the three horizontal taps of a tap row per block, with dz and a
+//   66-pixel input row loaded once and three tensor-memory accumulators.
 #pragma once
 
 #include <cuda.h>
