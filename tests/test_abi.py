@@ -109,3 +109,20 @@ def test_max_subsets_rule_on_the_papers_scanner():
     hel.pitch = 1.0
     assert math.floor(oslalm.max_subsets(hel, 24)) == 23
     assert abs(oslalm.max_subsets(hel, 24) * 2 - m05) < 1e-9
+
+
+def test_network_creation_validates_sizes_before_any_device_call(L):
+    """oslalm_cnn_create rejects sizes its kernels cannot take (not multiples
+    of 8; 2^31 pixels or more, the limit of the 32-bit pixel arithmetic of the
+    elementwise kernels) before it touches the device, and the network's
+    host-only entry points behave on NULL handles."""
+    h = ctypes.c_void_p()
+    assert L.oslalm_cnn_create(1, 12, 16, 0, ctypes.byref(h)) == -1  # height not a multiple of 8
+    assert b"multiples of 8" in L.oslalm_last_error()
+    assert L.oslalm_cnn_create(0, 16, 16, 0, ctypes.byref(h)) == -1
+    assert L.oslalm_cnn_create(8, 32768, 8192, 0, ctypes.byref(h)) == -1  # exactly 2^31 pixels
+    assert b"2^31" in L.oslalm_last_error()
+    assert h.value is None
+    assert L.oslalm_cnn_create(1, 16, 16, 0, None) == -1
+    assert L.oslalm_cnn_set_tma(None, 1) == -1
+    assert L.oslalm_cnn_launch_count() >= 0
